@@ -1,0 +1,291 @@
+"""Pins of the FP64 oracle: checks against what the model and the mathematics
+fix, independent of the oracle's own code.
+
+Each pin takes an ``oracle.Oracle`` and raises AssertionError on failure, so
+the same checks run against the real oracle (tests/test_oracle_pins.py) and
+against deliberately broken copies of it (tests/test_oracle_mutants.py).
+
+What each pin fixes:
+  rest_root            p(u*) = 0 for the cubic obtained by setting Eq. 1's
+                       bracket to zero with v = u; checked against
+                       numpy.roots (a library routine), not the oracle's
+                       bisection.
+  rest_fixed_point     a homogeneous field at u = v = u* does not move under
+                       the full step (uses the step's own reaction term, so
+                       it ties the step to the cubic).
+  jacobian             one step of a small perturbation of the rest state
+                       equals (I + dt J) applied to it, J the analytic
+                       Jacobian of Eq. 1's reaction part (derivatives taken by
+                       hand): pins eps scaling, the f v coupling, the sign of
+                       every reaction term and the v equation.
+  jacobian_with_mode   the same for a cosine-mode perturbation in the full
+                       model: I + dt (J + diag(Du lambda_k, 0)) -- pins how
+                       diffusion enters the full update.
+  cosine_modes         diffusion alone maps cos(pi k (j+1/2)/W) cos(pi l
+                       (i+1/2)/H) to (1 + dt Du lambda) times itself with
+                       lambda = -(4/dx^2)[sin^2(pi k/2W) + sin^2(pi l/2H)]:
+                       the eigenpairs of the five-node Laplacian under
+                       zero-flux (cell-centred mirror) borders.
+  conservation         diffusion alone conserves sum(u) (the mirror border
+                       has zero flux).
+  symmetry             a seed invariant under the 8 symmetries of the square
+                       stays exactly invariant.
+  one_d                rows that are identical stay identical and equal the
+                       1-row grid (the y-terms cancel exactly).
+  uniform_is_single    a uniform field of any value evolves like one cell.
+  spike                diffusion of a single spike on a 3 x 3 grid gives the
+                       textbook five-point weights (interior and corner).
+  gauss_circle         the number of lattice points in a disk of radius r
+                       about a lattice point is Gauss's N(r); an off-centre
+                       disk's centroid is its centre (axes not swapped).
+  health               a cell at the pole u = -q, or finite left of it, is
+                       reported at the right step and index.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Table 1
+EPS, F, PHI_A, PHI_P, Q, DU, DT, DX = 0.0243, 1.4, 0.054, 0.0975, 0.002, 0.45, 0.001, 0.25
+
+# Lattice points with i^2 + j^2 <= r^2 (Gauss circle problem), r = 0..10.
+GAUSS_N = [1, 5, 13, 29, 49, 81, 113, 149, 197, 253, 317]
+
+
+def _params(oracle_mod, flags=0, **kw):
+    return oracle_mod.Params(flags=flags, **kw)
+
+
+def cubic_root_numpy(phi, f=F, q=Q):
+    r = np.roots([1.0, f + q - 1.0, phi - q - f * q, -phi * q])
+    pos = [x.real for x in r if abs(x.imag) < 1e-12 and x.real > 0]
+    assert len(pos) == 1, f"expected one positive root, got {r}"
+    return pos[0]
+
+
+def cubic_root_exact(phi, f=F, q=Q):
+    """The positive root to 40 digits, coefficients taken exactly from the
+    doubles (sympy's arbitrary-precision root finder)."""
+    import pytest
+    sympy = pytest.importorskip("sympy")
+    from fractions import Fraction
+    x = sympy.Symbol("x")
+    fr = lambda d: sympy.Rational(Fraction(d))  # noqa: E731
+    fq, ff, fp = fr(q), fr(f), fr(phi)
+    poly = sympy.Poly(x ** 3 + (ff + fq - 1) * x ** 2 + (fp - fq - ff * fq) * x - fp * fq, x)
+    roots = [r for r in poly.nroots(n=40) if r.is_real and r > 0]
+    assert len(roots) == 1
+    return roots[0]
+
+
+def pin_rest_root(o, om):
+    for phi in (0.054, 0.0975, 0.2, 0.05, 0.08, 0.0301):
+        us = o.rest_state(phi)
+        ref = cubic_root_numpy(phi)
+        assert abs(us - ref) <= 4e-15 * ref, (phi, us, ref)
+        exact = cubic_root_exact(phi)
+        ulp = np.spacing(us)
+        assert abs(float(exact - us)) <= 2 * ulp, (phi, us, exact)
+
+
+def pin_rest_fixed_point(o, om):
+    phi = np.full((9, 16), PHI_A)
+    u, v = o.rest_field(phi)
+    us = u[0, 0]
+    r = o.run(phi, u, v, 20000, params=_params(om))
+    assert r["status"] == 0
+    assert np.max(np.abs(r["u"] - us)) <= 1e-12
+    assert np.max(np.abs(r["v"] - us)) <= 1e-12
+
+
+def analytic_jacobian(u, v, phi, f=F, q=Q, eps=EPS):
+    # R(u, v) = u - u^2 - (f v + phi)(u - q)/(u + q)
+    dR_du = 1.0 - 2.0 * u - (f * v + phi) * (2.0 * q) / (u + q) ** 2
+    dR_dv = -f * (u - q) / (u + q)
+    return np.array([[dR_du / eps, dR_dv / eps], [1.0, -1.0]])
+
+
+def pin_jacobian(o, om):
+    for phi in (PHI_A, PHI_P):
+        # linearise about a non-rest point as well, so the u^2 and v terms
+        # are weighted differently from the rest state
+        for (u0, v0) in ((o.rest_state(phi),) * 2, (0.3, 0.1)):
+            J = analytic_jacobian(u0, v0, phi)
+            A = np.eye(2) + DT * J
+            h = 1e-6
+            ph = np.full((1, 1), phi)
+            cols = []
+            for d in ((h, 0.0), (0.0, h)):
+                up = o.step(ph, np.full((1, 1), u0 + d[0]), np.full((1, 1), v0 + d[1]))
+                um = o.step(ph, np.full((1, 1), u0 - d[0]), np.full((1, 1), v0 - d[1]))
+                cols.append([(up[0][0, 0] - um[0][0, 0]) / (2 * h),
+                             (up[1][0, 0] - um[1][0, 0]) / (2 * h)])
+            num = np.array(cols).T
+            assert np.allclose(num, A, rtol=1e-6, atol=1e-7), (phi, u0, v0, num, A)
+
+
+def pin_jacobian_with_mode(o, om):
+    """Full model (reaction + diffusion): a small cosine-mode perturbation of
+    the rest state evolves by I + dt (J + diag(Du lambda_k, 0)) -- pins how the
+    diffusion term enters the full update."""
+    W, H = 12, 7
+    phi = PHI_A
+    us = o.rest_state(phi)
+    J = analytic_jacobian(us, us, phi)
+    for (k, l) in ((1, 0), (3, 2), (W - 1, H - 1)):
+        m = cosine_mode(W, H, k, l)
+        lam = -(4.0 / DX ** 2) * (math.sin(math.pi * k / (2 * W)) ** 2 +
+                                  math.sin(math.pi * l / (2 * H)) ** 2)
+        A = np.eye(2) + DT * (J + np.array([[DU * lam, 0.0], [0.0, 0.0]]))
+        h = 1e-7
+        ph = np.full((H, W), phi)
+        cols = []
+        for d in ((h, 0.0), (0.0, h)):
+            up = o.step(ph, us + d[0] * m, us + d[1] * m)
+            um = o.step(ph, us - d[0] * m, us - d[1] * m)
+            # project the response back onto the mode
+            nm = np.sum(m * m)
+            cols.append([np.sum((up[0] - um[0]) * m) / (2 * h * nm),
+                         np.sum((up[1] - um[1]) * m) / (2 * h * nm)])
+        num = np.array(cols).T
+        assert np.allclose(num, A, rtol=1e-5, atol=1e-6), (k, l, num, A)
+
+
+def cosine_mode(W, H, k, l):
+    j = np.arange(W)
+    i = np.arange(H)
+    return np.outer(np.cos(np.pi * l * (i + 0.5) / H), np.cos(np.pi * k * (j + 0.5) / W))
+
+
+def pin_cosine_modes(o, om):
+    W, H = 13, 8
+    p = _params(om, flags=om.DIFFUSION_ONLY)
+    for (k, l) in ((0, 0), (1, 0), (0, 1), (3, 2), (5, 7), (W - 1, H - 1), (W - 1, 0)):
+        m = cosine_mode(W, H, k, l)
+        u = 0.5 + 0.25 * m
+        lam = -(4.0 / DX ** 2) * (math.sin(math.pi * k / (2 * W)) ** 2 +
+                                  math.sin(math.pi * l / (2 * H)) ** 2)
+        expect = 0.5 + 0.25 * (1.0 + DT * DU * lam) * m
+        u1, _, rc, _ = o.step(np.full((H, W), PHI_A), u, u.copy(), p)
+        assert rc == 0
+        assert np.max(np.abs(u1 - expect)) <= 1e-13, (k, l, np.max(np.abs(u1 - expect)))
+
+
+def pin_conservation(o, om):
+    rng = np.random.default_rng(11)
+    W, H = 31, 17
+    u0 = rng.uniform(0.0, 0.8, size=(H, W))
+    p = _params(om, flags=om.DIFFUSION_ONLY)
+    r = o.run(np.full((H, W), PHI_A), u0, u0.copy(), 1000, params=p)
+    s0 = math.fsum(u0.ravel())
+    s1 = math.fsum(r["u"].ravel())
+    assert abs(s1 - s0) / s0 <= 1e-12, (s0, s1)
+    # and the field did diffuse
+    assert np.std(r["u"]) < 0.5 * np.std(u0)
+
+
+def pin_symmetry(o, om):
+    N = 40
+    phi = np.full((N, N), PHI_A)
+    u, v = o.rest_field(phi)
+    o.seed_disk(u, (N - 1) / 2, (N - 1) / 2, 6.0, 0.8)
+    r = o.run(phi, u, v, 400)
+    U = r["u"]
+    assert np.array_equal(U, U[::-1, :])
+    assert np.array_equal(U, U[:, ::-1])
+    assert np.array_equal(U, U.T)
+    assert U.max() > 0.3  # a wave was excited
+
+
+def pin_one_d(o, om):
+    W = 64
+    phi1 = np.full((1, W), PHI_A)
+    u1, v1 = o.rest_field(phi1)
+    u1[:, :4] = 0.8
+    r1 = o.run(phi1, u1, v1, 600)
+    phi5 = np.full((5, W), PHI_A)
+    u5, v5 = o.rest_field(phi5)
+    u5[:, :4] = 0.8
+    r5 = o.run(phi5, u5, v5, 600)
+    for i in range(5):
+        assert np.array_equal(r5["u"][i], r1["u"][0])
+        assert np.array_equal(r5["v"][i], r1["v"][0])
+    assert r1["u"][0, 20] > 0.3 or r1["u"][0, 10] > 0.3  # the front travelled
+
+
+def pin_uniform_is_single(o, om):
+    for val in (0.2, 0.6):
+        phi = np.full((6, 7), PHI_A)
+        u = np.full((6, 7), val)
+        v = np.full((6, 7), 0.05)
+        r = o.run(phi, u, v, 300)
+        r1 = o.run(phi[:1, :1], u[:1, :1], v[:1, :1], 300)
+        assert np.all(r["u"] == r1["u"][0, 0]) and np.all(r["v"] == r1["v"][0, 0])
+
+
+def pin_spike(o, om):
+    a = DT * DU / DX ** 2
+    p = _params(om, flags=om.DIFFUSION_ONLY)
+    # interior spike: centre loses 4a, each of the 4 neighbours gains a
+    u = np.zeros((3, 3))
+    u[1, 1] = 1.0
+    u1, _, _, _ = o.step(np.full((3, 3), PHI_A), u, u.copy(), p)
+    exp = np.zeros((3, 3))
+    exp[1, 1] = 1.0 - 4 * a
+    exp[0, 1] = exp[2, 1] = exp[1, 0] = exp[1, 2] = a
+    assert np.max(np.abs(u1 - exp)) <= 1e-15
+    # corner spike: the mirror ghosts are the corner itself, so it loses 2a
+    u = np.zeros((3, 3))
+    u[0, 0] = 1.0
+    u1, _, _, _ = o.step(np.full((3, 3), PHI_A), u, u.copy(), p)
+    exp = np.zeros((3, 3))
+    exp[0, 0] = 1.0 - 2 * a
+    exp[0, 1] = exp[1, 0] = a
+    assert np.max(np.abs(u1 - exp)) <= 1e-15
+
+
+def pin_gauss_circle(o, om):
+    N = 41
+    for r, expect in enumerate(GAUSS_N):
+        u = np.zeros((N, N))
+        n = o.seed_disk(u, 20.0, 20.0, float(r), 1.0)
+        assert n == expect and int(u.sum()) == expect, (r, n, expect)
+    # half-integer centre: symmetric under the square's symmetries, and
+    # clipped at the border
+    u = np.zeros((8, 8))
+    o.seed_disk(u, 3.5, 3.5, 2.0, 1.0)
+    assert np.array_equal(u, u.T) and np.array_equal(u, u[::-1, ::-1])
+    assert int(u.sum()) == 12  # (+-1/2, +-1/2) x4, (+-3/2, +-1/2) x8
+    u = np.zeros((5, 5))
+    assert o.seed_disk(u, 0.0, 0.0, 1.0, 1.0) == 3
+    # an off-centre disk on a non-square grid: x is the column, y the row,
+    # and a lattice disk about a lattice point has its centroid at the centre
+    u = np.zeros((30, 17))
+    n = o.seed_disk(u, 5.0, 12.0, 4.0, 1.0)
+    ii, jj = np.nonzero(u)
+    assert n == GAUSS_N[4] and ii.mean() == 12.0 and jj.mean() == 5.0
+
+
+def pin_health(o, om):
+    phi = np.full((4, 5), PHI_A)
+    u, v = o.rest_field(phi)
+    u[2, 3] = -Q            # exactly at the pole
+    r = o.run(phi, u, v, 10)
+    assert r["status"] == om.ENONFINITE and r["bad_step"] == 1 and r["bad_index"] == 2 * 5 + 3
+    # finite but left of the pole: u + q < 0 must be reported too
+    u, v = o.rest_field(phi)
+    u[1, 4] = -0.01
+    r = o.run(phi, u, v, 10)
+    assert r["status"] == om.ENONFINITE and r["bad_step"] == 1 and r["bad_index"] == 1 * 5 + 4
+    assert np.isfinite(r["u"]).all()
+    u, v = o.rest_field(phi)
+    r = o.run(phi, u, v, 10)
+    assert r["status"] == 0 and r["bad_step"] == -1
+
+
+ALL_PINS = [pin_rest_root, pin_rest_fixed_point, pin_jacobian, pin_jacobian_with_mode,
+            pin_cosine_modes,
+            pin_conservation, pin_symmetry, pin_one_d, pin_uniform_is_single, pin_spike,
+            pin_gauss_circle, pin_health]

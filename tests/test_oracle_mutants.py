@@ -1,0 +1,64 @@
+"""Each plausible mistake planted in a copy of the oracle (on the CPU) must
+fail at least one pin: a dropped term, a wrong sign, a wrong index, a wrong
+border rule, a transposed or swapped operand.  The real oracle is never
+modified; every mutant is compiled to a temporary library."""
+from __future__ import annotations
+
+import os
+
+import pytest
+
+import oracle
+from tests import oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "rdc_oracle.c")
+
+# (name, original text, replacement)
+MUTANTS = [
+    ("ratio_inverted", "(c - q) / (c + q)", "(c + q) / (c - q)"),
+    ("ratio_sign", "(c - q) / (c + q)", "(c + q) / (c + q)"),
+    ("phi_sign", "(f * vc + phi[k])", "(f * vc - phi[k])"),
+    ("fv_dropped", "(f * vc + phi[k])", "(phi[k])"),
+    ("eps_multiplies", "du = R / eps + Du * lap;", "du = R * eps + Du * lap;"),
+    ("Du_dropped", "du = R / eps + Du * lap;", "du = R / eps + lap;"),
+    ("quadratic_sign", "(c - c * c)", "(c + c * c)"),
+    ("quadratic_dropped", "(c - c * c)", "(c)"),
+    ("v_sign", "vc + dt * (c - vc)", "vc + dt * (vc - c)"),
+    ("v_uses_new_u", "v1[k] = vc + dt * (c - vc);", "v1[k] = vc + dt * (un - vc);"),
+    ("dt_dropped", "const double un = c + dt * du;", "const double un = c + du * 0.01;"),
+    ("centre_weight", "- 4.0 * c)", "- 3.0 * c)"),
+    ("dx_not_squared", "1.0 / (p->dx * p->dx)", "1.0 / p->dx"),
+    ("south_wraps", "(i < H - 1) ? i + 1 : H - 1", "(i < H - 1) ? i + 1 : 0"),
+    ("east_vertex_mirror", "(j < W - 1) ? j + 1 : W - 1", "(j < W - 1) ? j + 1 : W - 2"),
+    ("north_index_swapped", "u[(int64_t)in * W + j]", "u[(int64_t)i * W + jw]"),
+    ("south_uses_north", "u[(int64_t)is * W + j]", "u[(int64_t)in * W + j]"),
+    ("rows_cols_transposed", "const double e = u[(int64_t)i * W + je];",
+     "const double e = u[(int64_t)(je < H ? je : H - 1) * W + i % W];"),
+    ("rest_a1_sign", "const double a1 = (phi - q) - f * q;", "const double a1 = (phi + q) - f * q;"),
+    ("rest_a0_dropped", "const double a0 = -(phi * q);", "const double a0 = 0.0 * q;"),
+    ("seed_strict", "if (dy * dy + dx * dx <= r2)", "if (dy * dy + dx * dx < r2)"),
+    ("seed_axes_swapped", "double dy = (double)i - cy;", "double dy = (double)i - cx;"),
+    ("health_no_pole", "|| (u + q) <= 0.0;", "|| 0;"),
+]
+
+
+def _pins_fail(o) -> list[str]:
+    failed = []
+    for pin in P.ALL_PINS:
+        try:
+            pin(o, oracle)
+        except (AssertionError, ValueError):
+            failed.append(pin.__name__)
+    return failed
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(name, old, new, tmp_path):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    mutated = src.replace(old, new)
+    path = tmp_path / "mut.c"
+    path.write_text(mutated)
+    lib = oracle.compile_oracle(str(path), str(tmp_path / f"lib{name}.so"), openmp=False)
+    failed = _pins_fail(oracle.Oracle(lib))
+    assert failed, f"mutant {name} passed every pin"
