@@ -1,0 +1,370 @@
+"""Benchmark of the Oregonator time-stepper (GCUPS and fraction of HBM roofline).
+
+Workload (one bench step = one pass of the whole hot path over one input):
+  8192 x 8192 grid, Table 1 kinetics, uniform phi = 0.054 plus 200 seeded
+  u = 0.8 disks (radius U{4..10}, centres uniform, PCG64 seed 3), FP32 compute
+  and storage: stimulate the 200 disks, advance 10000 explicit Euler steps
+  with the single-step kernel, run the health check.  The state (1.34 GB)
+  is far larger than L2 (129 MB), so no flush is needed between steps.
+
+The JSON line also reports temporal blocking (k steps per launch) and the
+reduced-storage modes as effective GCUPS on the same grid, the end-to-end
+rate through the C ABI with host buffers (phi in, state out, every step),
+and the FP64 oracle timed on the host cores as a baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs its own independent copy of the
+workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rdc_inputs as ri  # noqa: E402
+
+W = H = 8192
+EULER_STEPS = 10000
+N_DISKS = 200
+DISK_SEED = 3
+BYTES_PER_CELL = {"f32": 20, "bf16": 12, "f16": 12, "f64": 40}
+METRIC = "GCUPS (cell-updates/s)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_gcups(target_s: float = 15.0, steps: int | None = None):
+    """Times the FP64 oracle on the host cores on the 8192^2 workload for a
+    bounded number of Euler steps; returns (gcups, threads, steps)."""
+    import oracle
+    orc = oracle.load()
+    threads = os.cpu_count() or 1
+    phi = np.full((H, W), ri.PHI_ACTIVE)
+    us = orc.rest_state(ri.PHI_ACTIVE)
+    u = np.full((H, W), us)
+    v = u.copy()
+    for (cx, cy, r) in ri.random_disks(DISK_SEED, N_DISKS, W, H):
+        orc.seed_disk(u, cx, cy, r, ri.SEED_VALUE)
+    if steps is None:
+        t0 = time.perf_counter()
+        orc.run(phi, u, v, 1, nthreads=threads)
+        one = time.perf_counter() - t0
+        steps = max(1, int(target_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    orc.run(phi, u, v, steps, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return W * H * steps / dt / 1e9, threads, steps
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each "step" of the reference arm: the oracle on the full grid for a
+    # bounded number of Euler steps (sized so the whole run stays short)
+    gc, threads, steps = oracle_gcups(target_s=8.0)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        g, _, _ = oracle_gcups(steps=steps)
+        if i >= args.warmup:
+            vals.append(g)
+    value = float(np.median(vals)) if vals else gc
+    sample = f"FP64 oracle, {W}x{H} grid, {steps} Euler steps per bench step, {threads} threads"
+    line = {"metric": METRIC, "value": value, "unit": "GCUPS", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"oregonator_{W}x{H}_phi0.054_200disks", "grid": [W, H],
+                       "euler_steps_per_bench_step": steps, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--euler-steps", type=int, default=EULER_STEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the temporal-blocking / storage-mode / e2e lines")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="square grid size (default 8192); smaller sizes are for profiling")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.grid:
+        global W, H
+        W = H = int(args.grid)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_1901_06535_gb300 as pkg
+    pkg.lib()
+
+    # a dedicated stream: the simulation and the CUDA events share it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    p = pkg.rdc_params_default(precision=pkg.RDC_F32, k_block=1)
+    h = pkg.rdc_create(W, H, p, None, stream.cuda_stream)
+    disks = ri.random_disks(DISK_SEED, N_DISKS, W, H)
+    nE = args.euler_steps
+
+    def one_step(ev=None):
+        for (cx, cy, r) in disks:
+            pkg.rdc_seed(h, cx, cy, r, ri.SEED_VALUE)
+        if ev is not None:
+            ev[0].record(stream)
+        pkg.rdc_step(h, nE)
+        if ev is not None:
+            ev[1].record(stream)
+        rc, _ = pkg.rdc_check(h)
+        return rc
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    launches0 = pkg.rdc_get_view(h).launches
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    statuses = [one_step(evs[i]) for i in range(args.steps)]
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    step_kernel_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    launches = pkg.rdc_get_view(h).launches - launches0
+    t_max = max_over_ranks(elapsed, world)
+
+    cells = W * H * nE * args.steps
+    value = world * cells / t_max / 1e9
+    ms_per_step = t_max / args.steps * 1e3
+    peak, peak_kind = _peaks()
+    per_launch_s = step_kernel_s / launches
+    bytes_per_launch = BYTES_PER_CELL["f32"] * W * H
+    achieved = bytes_per_launch / per_launch_s / 1e9
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # temporal blocking and storage modes: effective GCUPS on the same grid
+        tb = {}
+        for k in (1, 2, 4, 8):
+            tb[str(k)] = _mode_gcups(pkg, stream, "f32", k, 1000)
+        modes = {m: _mode_gcups(pkg, stream, m, 1, 1000) for m in ("bf16", "f16")}
+        modes["bf16_k4"] = _mode_gcups(pkg, stream, "bf16", 4, 1000)
+        modes["f64"] = _mode_gcups(pkg, stream, "f64", 1, 100)
+        extras = {"temporal_blocking_gcups": tb, "storage_modes_gcups": modes}
+    e2e = None if args.no_extras else _e2e(pkg, stream, h, disks, nE, args)
+
+    pkg.rdc_destroy(h)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, threads, steps = oracle_gcups(target_s=15.0)
+        cpu = {"value": g, "unit": "GCUPS", "cores": threads, "kind": "oracle",
+               "sample": f"FP64 oracle on the same {W}x{H} workload, {steps} Euler steps, "
+                         f"{threads} host threads"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"oregonator_{W}x{H}_phi0.054_200disks",
+                           "grid": [W, H], "euler_steps_per_bench_step": nE,
+                           "kernel": "single-step (k=1)", "precision": "f32",
+                           "l2": "inputs larger than L2 (1.34 GB state), no flush"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak,
+                             "peak_kind": peak_kind, "traffic": None,
+                             "kernel": "k_step1<float>",
+                             "bytes_per_cell_update": BYTES_PER_CELL["f32"],
+                             "launch_us": per_launch_s * 1e6},
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches + args.steps * (N_DISKS + 1)),
+                "health": [int(s) for s in statuses]}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _mode_gcups(pkg, stream, mode, k, n):
+    import torch
+    prec = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}[mode]
+    p = pkg.rdc_params_default(precision=prec, k_block=k)
+    h = pkg.rdc_create(W, H, p, None, stream.cuda_stream)
+    try:
+        pkg.rdc_seed(h, W / 2, H / 2, 10.0, 0.8)
+        pkg.rdc_step(h, 3 * k)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        pkg.rdc_step(h, n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return W * H * n / (a.elapsed_time(b) / 1e3) / 1e9
+    finally:
+        pkg.rdc_destroy(h)
+
+
+def _e2e(pkg, stream, h, disks, nE, args):
+    """Same metric through the C ABI with host buffers: each step uploads the
+    phi map (pinned host memory; the library resets to the rest state),
+    stimulates, steps, and reads u and v back into pinned host memory."""
+    import torch
+    phi = torch.full((H, W), ri.PHI_ACTIVE, dtype=torch.float32).pin_memory()
+    uo = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    vo = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    steps = max(1, min(args.steps, 3))
+    times = []
+    for i in range(1 + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pkg.rdc_set_phi(h, phi)
+        for (cx, cy, r) in disks:
+            pkg.rdc_seed(h, cx, cy, r, ri.SEED_VALUE)
+        pkg.rdc_step(h, nE)
+        pkg.rdc_read(h, uo, vo)
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times[1:]))
+    return {"value": W * H * nE / t / 1e9, "unit": "GCUPS",
+            "h2d_bytes_per_step": W * H * 4 + 0, "d2h_bytes_per_step": 2 * W * H * 4,
+            "steps": steps}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,296 @@
+/*
+ * rdc.h -- C ABI of librdc, a GPU (sm_103a) time-stepper for the
+ * two-variable Oregonator reaction-diffusion model.
+ *
+ * The model (Eq. 1, §2 of "RDCSim: a GPU-Accelerated, Interactive Simulator
+ * for Reaction-Diffusion Chemistry"):
+ *
+ *     u_t = (1/eps) [ u - u^2 - (f v + phi(x,y)) (u - q)/(u + q) ] + Du lap(u)
+ *     v_t = u - v
+ *
+ * integrated with explicit forward Euler (timestep dt) and the five-node
+ * discrete Laplacian on a square grid of spacing dx (§2, the paragraph after
+ * Table 1); phi is a per-cell excitability map (§2, §3: active and passive
+ * substrate).  Defaults are Table 1.  Catalytic stimulation sets u of the
+ * stimulated cells to a value (§2).
+ *
+ * Points the paper leaves open are fixed as follows, and every kernel
+ * behind this header follows them:
+ *   - zero-flux borders: a neighbour outside the grid takes the value of
+ *     the border cell itself (cell-centred mirror);
+ *   - Jacobi update: u' and v' are both computed from step n;
+ *   - initial state: u = v = u*(phi) per cell, the homogeneous rest state;
+ *   - Laplacian summed as ((w + e) + (n + s)) - 4 c, scaled by 1/(dx*dx);
+ *   - no clamping of u or v.
+ *
+ * Conventions for every call:
+ *   - Each call returns an int status (RDC_OK = 0 on success).  Invalid
+ *     arguments return RDC_EINVAL and change nothing.
+ *   - Grids are H rows by W columns, row-major; cell (i, j) is row i (y),
+ *     column j (x); host arrays are packed (row stride W elements).
+ *   - Host input buffers are copied before the call returns; the caller
+ *     owns all host buffers.  Device memory belongs to the library except
+ *     with rdc_create_ext, where the caller owns it and must keep it alive
+ *     until rdc_destroy.
+ *   - All device work of a simulation runs on its CUDA stream, in call
+ *     order.  Calls marked "async" only enqueue work; calls that return
+ *     host data synchronise that stream.
+ *   - A handle is not thread-safe; distinct handles may be used from
+ *     distinct threads.
+ */
+#ifndef RDC_H_
+#define RDC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RDC_OK 0
+#define RDC_EINVAL 1          /* invalid argument; nothing was changed */
+#define RDC_ENOMEM 2          /* a device or host allocation failed */
+#define RDC_ECUDA 3           /* a CUDA call failed (message: rdc_last_error) */
+#define RDC_ENONFINITE 4      /* the state holds a non-finite u or u + q <= 0 */
+#define RDC_ETIMEOUT 5        /* a bounded device wait gave up */
+#define RDC_EUNSTABLE_WARN 6  /* informational: forward Euler is linearly
+                                 unstable at the rest state of some phi */
+#define RDC_EUNSUPPORTED 7    /* valid request this build cannot serve */
+
+/* ---- precision modes ---------------------------------------------------- */
+/* Arithmetic and storage of u, v (and phi) on the device. */
+#define RDC_F32 0             /* FP32 compute, FP32 u/v/phi (20 B per cell-update) */
+#define RDC_F64 1             /* FP64 compute and storage; op order identical to
+                                 the sequence documented at rdc_step, with no
+                                 contraction, so results are bit-reproducible
+                                 against any IEEE FP64 implementation of it */
+#define RDC_F32_BF16STORE 2   /* FP32 compute, u/v stored as bfloat16 (RN-even),
+                                 phi FP32 (12 B per cell-update) */
+#define RDC_F32_F16STORE 3    /* FP32 compute, u/v stored as IEEE half (RN-even),
+                                 phi FP32 */
+
+/* ---- host buffer element types ------------------------------------------ */
+#define RDC_DTYPE_F32 0
+#define RDC_DTYPE_F64 1
+#define RDC_DTYPE_BF16 2
+#define RDC_DTYPE_F16 3
+
+/* ---- flags (test modes; 0 = the full model) ------------------------------ */
+#define RDC_DIFFUSION_ONLY 1  /* drop the reaction term from u_t */
+#define RDC_REACTION_ONLY 2   /* drop Du lap(u) from u_t */
+
+typedef struct rdc_sim rdc_sim; /* opaque simulation handle */
+
+typedef struct {
+    int32_t width;   /* W, columns (x), >= 1 */
+    int32_t height;  /* H, rows (y), >= 1 */
+} rdc_grid;
+
+/* Model and run parameters.  rdc_params_default fills Table 1. */
+typedef struct {
+    double eps;        /* epsilon, time-scale ratio            (Table 1: 0.0243) */
+    double f;          /* stoichiometric factor                (Table 1: 1.4)    */
+    double q;          /* propagation scaling factor           (Table 1: 0.002)  */
+    double Du;         /* diffusion coefficient of u           (Table 1: 0.45)   */
+    double dt;         /* Euler timestep                       (Table 1: 0.001)  */
+    double dx;         /* grid spacing                         (Table 1: 0.25)   */
+    int32_t precision; /* RDC_F32 / RDC_F64 / RDC_F32_BF16STORE / RDC_F32_F16STORE */
+    int32_t flags;     /* RDC_DIFFUSION_ONLY | RDC_REACTION_ONLY (not both) */
+    int32_t k_block;   /* Euler steps fused per launch (temporal blocking):
+                          0 = library default, 1 = one step per launch,
+                          2..8 = k steps per launch.  Results are bitwise
+                          identical for every k. */
+    int32_t reserved;  /* must be 0 */
+} rdc_params;
+
+/* Fills *out with Table 1 (eps, f, q, Du, dt, dx), RDC_F32, flags 0,
+ * k_block 0.  Returns RDC_EINVAL if out is NULL. */
+int rdc_params_default(rdc_params* out);
+
+/*
+ * Creates a simulation of grid g and sets it to the rest state
+ * u = v = u*(phi) of every cell (see rdc_rest_state).
+ *   phi_host : H*W floats, row-major, copied; NULL = uniform phi_active
+ *              (Table 1: 0.054).  Each value must be finite and exceed
+ *              q (1 + f) so that a positive rest state exists.
+ *   stream   : a cudaStream_t to run on (cudaStreamLegacy and
+ *              cudaStreamPerThread are accepted), or NULL for a
+ *              library-owned non-blocking stream.  A caller's stream must
+ *              outlive the simulation.
+ *   out      : receives the handle; *out is NULL on failure.
+ * Validation (RDC_EINVAL): W or H < 1; a non-finite parameter; eps, q, dt
+ * or dx <= 0; Du < 0; f + q <= 1; Du dt / dx^2 > 1/4 (the explicit
+ * diffusion limit); both test flags set; k_block outside 0..8; reserved != 0.
+ * The device must be sm_103 (RDC_EUNSUPPORTED otherwise).
+ */
+int rdc_create(rdc_grid g, const rdc_params* p, const float* phi_host,
+               void* stream, rdc_sim** out);
+
+/* As rdc_create with a double-precision phi map (for RDC_F64 parity runs;
+ * in FP32 modes the values are rounded to float). */
+int rdc_create_f64phi(rdc_grid g, const rdc_params* p, const double* phi_host,
+                      void* stream, rdc_sim** out);
+
+/*
+ * As rdc_create, on caller-owned device memory (for example torch tensors).
+ *   dev_u[2], dev_v[2] : two state buffers each (ping-pong), storage type of
+ *                        p->precision, row pitch pitch_bytes;
+ *   dev_phi            : phi map, float (double for RDC_F64), same pitch in
+ *                        elements as the state planes: pitch_bytes / sizeof
+ *                        of the state element;
+ *   pitch_bytes        : a multiple of 16 bytes, >= W * element size.
+ * All pointers must be 16-byte aligned.  The state is NOT initialised: the
+ * current state is dev_u[0], dev_v[0] as the caller left it (use
+ * rdc_reset_rest to set the rest state).  The library never frees them.
+ */
+int rdc_create_ext(rdc_grid g, const rdc_params* p, void* const dev_u[2],
+                   void* const dev_v[2], const void* dev_phi,
+                   size_t pitch_bytes, void* stream, rdc_sim** out);
+
+/* Destroys the handle and frees library-owned memory; waits for the
+ * simulation's stream first.  NULL is a no-op. */
+void rdc_destroy(rdc_sim* sim);
+
+/* Async.  Replaces the phi map (host, H*W of dtype RDC_DTYPE_F32 or
+ * RDC_DTYPE_F64) and resets the state to the rest state of the new map. */
+int rdc_set_phi(rdc_sim* sim, const void* phi_host, int32_t dtype);
+
+/* Async.  Sets u = v = u*(phi) per cell from the current phi map. */
+int rdc_reset_rest(rdc_sim* sim);
+
+/*
+ * Async.  Catalytic stimulation (§2): u := value (rounded to the storage
+ * type) for every cell (i, j) with (i - cy)^2 + (j - cx)^2 <= r^2, the
+ * squares and the sum taken in FP64 round-to-nearest with no contraction;
+ * v is unchanged.  cx is the column coordinate, cy the row coordinate, cell
+ * centres at integers.  Requires finite cx, cy, value and 0 <= r < 2^24;
+ * cells outside the grid are skipped.
+ */
+int rdc_seed(rdc_sim* sim, double cx, double cy, double r, double value);
+
+/* Async w.r.t. the device, but the host buffers are consumed before
+ * return.  Sets the current state from packed H*W host arrays of dtype
+ * (rounded RN-even to the storage type); u or v may be NULL to leave that
+ * plane unchanged. */
+int rdc_set_state(rdc_sim* sim, const void* u_host, const void* v_host,
+                  int32_t dtype);
+
+/*
+ * Async.  Advances the state by n >= 0 explicit Euler steps.  Per cell, with
+ * c, w, e, n_, s the current u at the cell and its west, east, north and
+ * south neighbours (mirrored at the borders) and v, phi the cell's values:
+ *     lap = (((w + e) + (n_ + s)) - 4 c) * (1 / (dx*dx))
+ *     rat = (c - q) / (c + q)
+ *     R   = (c - c*c) - (f*v + phi) * rat
+ *     u'  = c + dt * (R/eps + Du*lap)     (flags drop one of the two terms)
+ *     v'  = v + dt * (c - v)
+ * RDC_F64 evaluates exactly this sequence in FP64 with IEEE division and no
+ * fused multiply-add.  The FP32 modes evaluate it in FP32 with IEEE
+ * division and a fixed set of fused multiply-adds, and round u', v' to the
+ * storage type after every step.  Every k_block and launch shape gives the
+ * same bits.
+ */
+int rdc_step(rdc_sim* sim, int64_t n);
+
+/*
+ * Synchronous.  Copies the current state into packed H*W host arrays of
+ * dtype (RDC_DTYPE_*; values are converted from the storage type, RN-even
+ * where narrowing); u_out or v_out may be NULL to skip.  Also runs the
+ * health check of rdc_check and returns RDC_ENONFINITE when it fails (the
+ * buffers are still filled).
+ */
+int rdc_read(rdc_sim* sim, void* u_out, void* v_out, int32_t dtype);
+
+/*
+ * Synchronous.  Health check: returns RDC_ENONFINITE if any cell's u is
+ * non-finite or has u + q <= 0 (the pole of (u - q)/(u + q) in Eq. 1),
+ * evaluated in the compute precision; *first_bad (optional) receives the
+ * smallest flat index i*W + j of such a cell, or -1.
+ */
+int rdc_check(rdc_sim* sim, int64_t* first_bad);
+
+/* Synchronous.  Reads u at n cells given as flat indices i*W + j into out
+ * (as double).  Any index outside [0, W*H) gives RDC_EINVAL. */
+int rdc_probe(rdc_sim* sim, int32_t n, const int64_t* cells, double* out);
+
+/* Waits until all work enqueued on the simulation's stream is done. */
+int rdc_sync(rdc_sim* sim);
+
+/*
+ * Rest state used by the initial condition: the positive root of
+ *     p(u) = u^3 + (f + q - 1) u^2 + (phi - q - f q) u - phi q,
+ * which is Eq. 1's reaction bracket with v = u, times (u + q).  Found by
+ * bisection on [0, 1] with a2 = (f + q) - 1, a1 = (phi - q) - f*q,
+ * a0 = -(phi*q), p(x) = ((x + a2)*x + a1)*x + a0 in FP64 without
+ * contraction, midpoint lo + (hi - lo)*0.5, lo := mid if p(mid) < 0 else
+ * hi := mid, until the midpoint equals an end; the result is hi.  The device
+ * initialiser uses the same rule, bit for bit.  RDC_EINVAL unless
+ * 0 < q < 1, f + q > 1 and phi > q (1 + f).
+ */
+int rdc_rest_state(double phi, double f, double q, double* u_star);
+
+/*
+ * Linear stability of forward Euler at the rest state of the largest phi
+ * in the map: *rho receives max |1 + dt lambda| over the eigenvalues lambda
+ * of the reaction Jacobian shifted by the discrete Laplacian's spectrum
+ * (from 0 to -8 Du / dx^2).  Returns RDC_EUNSTABLE_WARN when rho > 1 (the
+ * homogeneous state then oscillates with period 2 instead of resting), else
+ * RDC_OK.  (Table 1's phi_active gives rho < 1; phi = 0.2 gives rho > 1.)
+ */
+int rdc_stability(rdc_sim* sim, double* rho);
+
+/* Device-side view of the current state, for zero-copy access (e.g. from
+ * torch).  Pointers stay valid until the next rdc_step / rdc_destroy; the
+ * current buffer alternates between the two ping-pong planes. */
+typedef struct {
+    void* u;              /* current u plane */
+    void* v;              /* current v plane */
+    const void* phi;      /* phi plane (float, or double for RDC_F64) */
+    size_t pitch_bytes;   /* row stride of the state planes */
+    size_t phi_pitch_bytes;
+    int32_t width, height;
+    int32_t precision;
+    int32_t elem_bytes;   /* bytes per stored u or v value */
+    int64_t steps_done;   /* Euler steps applied since create / reset */
+    int64_t launches;     /* step-kernel launches enqueued so far */
+    void* stream;         /* the simulation's cudaStream_t */
+} rdc_view;
+
+int rdc_get_view(rdc_sim* sim, rdc_view* out);
+
+/* Launch shapes of the step kernels.  They change speed only: results are
+ * bitwise identical for every valid shape (each cell always runs the same
+ * operation sequence on the same inputs). */
+typedef struct {
+    int32_t bx;        /* single-step kernel: threads per CTA along x, a
+                          multiple of 32 in [32, 256]; each thread owns one
+                          16-byte vector of cells (4 FP32, 2 FP64, 8 BF16/FP16) */
+    int32_t rows;      /* single-step kernel: rows marched per CTA, >= 1 */
+    int32_t tx, ty;    /* temporally blocked kernel: interior tile, >= 1 each */
+    int32_t nthreads;  /* temporally blocked kernel: threads per CTA, a
+                          multiple of 32 in [32, 512] */
+    int32_t k;         /* Euler steps per launch, 1..8 (1 = single-step
+                          kernel only); the tile's shared memory,
+                          4 (tx + 2k)(ty + 2k) values, must fit in 227 KB */
+} rdc_launch_shape;
+
+/* Current launch shapes (set at create from the grid size and k_block). */
+int rdc_get_shape(rdc_sim* sim, rdc_launch_shape* out);
+
+/* Replaces the launch shapes; RDC_EINVAL (and no change) if out of range. */
+int rdc_set_shape(rdc_sim* sim, const rdc_launch_shape* in);
+
+/* Human-readable name of a status code (static storage). */
+const char* rdc_status_str(int status);
+
+/* Message of the last CUDA failure seen on this thread (static storage, ""
+ * if none). */
+const char* rdc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDC_H_ */

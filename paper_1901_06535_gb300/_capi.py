@@ -1,0 +1,345 @@
+"""ctypes binding of librdc (``include/rdc.h``): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the model: all work runs in librdc's CUDA kernels.  Host arrays
+may be NumPy arrays or CPU torch tensors (for bfloat16); device pointers and
+streams are plain integers (``tensor.data_ptr()``, ``stream.cuda_stream``).
+
+The library must have been built (``paper_1901_06535_gb300.build.build()``);
+importing this module without it raises immediately -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+RDC_OK = 0
+RDC_EINVAL = 1
+RDC_ENOMEM = 2
+RDC_ECUDA = 3
+RDC_ENONFINITE = 4
+RDC_ETIMEOUT = 5
+RDC_EUNSTABLE_WARN = 6
+RDC_EUNSUPPORTED = 7
+
+RDC_F32 = 0
+RDC_F64 = 1
+RDC_F32_BF16STORE = 2
+RDC_F32_F16STORE = 3
+
+RDC_DTYPE_F32 = 0
+RDC_DTYPE_F64 = 1
+RDC_DTYPE_BF16 = 2
+RDC_DTYPE_F16 = 3
+
+RDC_DIFFUSION_ONLY = 1
+RDC_REACTION_ONLY = 2
+
+PRECISION_NAMES = {"f32": RDC_F32, "f64": RDC_F64, "bf16": RDC_F32_BF16STORE,
+                   "f16": RDC_F32_F16STORE}
+
+
+class rdc_grid(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class rdc_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("f", ctypes.c_double),
+                ("q", ctypes.c_double), ("Du", ctypes.c_double),
+                ("dt", ctypes.c_double), ("dx", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("k_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rdc_view(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("phi", ctypes.c_void_p), ("pitch_bytes", ctypes.c_size_t),
+                ("phi_pitch_bytes", ctypes.c_size_t), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("elem_bytes", ctypes.c_int32), ("steps_done", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class rdc_launch_shape(ctypes.Structure):
+    _fields_ = [("bx", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("tx", ctypes.c_int32), ("ty", ctypes.c_int32),
+                ("nthreads", ctypes.c_int32), ("k", ctypes.c_int32)]
+
+
+class RdcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {rdc_status_str(status)}"
+        last = rdc_last_error()
+        if last:
+            msg += f" [{last}]"
+        super().__init__(msg)
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+# C signatures: name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "rdc_params_default": (ctypes.c_int, [ctypes.POINTER(rdc_params)]),
+    "rdc_create": (ctypes.c_int, [rdc_grid, ctypes.POINTER(rdc_params), _P, _P, ctypes.POINTER(_P)]),
+    "rdc_create_f64phi": (ctypes.c_int, [rdc_grid, ctypes.POINTER(rdc_params), _P, _P, ctypes.POINTER(_P)]),
+    "rdc_create_ext": (ctypes.c_int, [rdc_grid, ctypes.POINTER(rdc_params), ctypes.POINTER(_P),
+                                      ctypes.POINTER(_P), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "rdc_destroy": (None, [_P]),
+    "rdc_set_phi": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "rdc_reset_rest": (ctypes.c_int, [_P]),
+    "rdc_seed": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "rdc_set_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+    "rdc_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "rdc_read": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+    "rdc_check": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "rdc_probe": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "rdc_sync": (ctypes.c_int, [_P]),
+    "rdc_rest_state": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "rdc_stability": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "rdc_get_view": (ctypes.c_int, [_P, ctypes.POINTER(rdc_view)]),
+    "rdc_get_shape": (ctypes.c_int, [_P, ctypes.POINTER(rdc_launch_shape)]),
+    "rdc_set_shape": (ctypes.c_int, [_P, ctypes.POINTER(rdc_launch_shape)]),
+    "rdc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "rdc_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded librdc (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"librdc.so is not built at {path}; call "
+                    "paper_1901_06535_gb300.build.build() (needs nvcc)")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+        return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _host_ptr(a, what: str):
+    """(pointer, dtype code, shape) of a C-contiguous host array or tensor."""
+    if a is None:
+        return None, None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):   # torch tensor
+        import torch
+        if a.is_cuda:
+            raise ValueError(f"{what}: expected a host tensor")
+        if not a.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        codes = {torch.float32: RDC_DTYPE_F32, torch.float64: RDC_DTYPE_F64,
+                 torch.bfloat16: RDC_DTYPE_BF16, torch.float16: RDC_DTYPE_F16}
+        if a.dtype not in codes:
+            raise ValueError(f"{what}: unsupported dtype {a.dtype}")
+        return a.data_ptr(), codes[a.dtype], tuple(a.shape)
+    a = np.asarray(a)
+    if not a.flags.c_contiguous:
+        raise ValueError(f"{what}: array must be C-contiguous")
+    codes = {np.dtype(np.float32): RDC_DTYPE_F32, np.dtype(np.float64): RDC_DTYPE_F64,
+             np.dtype(np.float16): RDC_DTYPE_F16}
+    if a.dtype not in codes:
+        raise ValueError(f"{what}: unsupported dtype {a.dtype}")
+    return a.ctypes.data, codes[a.dtype], a.shape
+
+
+CUDA_STREAM_LEGACY = 0x1
+
+
+def _stream(stream):
+    """None -> NULL (a library-owned stream).  0, torch's handle for the
+    default stream, maps to cudaStreamLegacy so that the work stays ordered
+    with it instead of silently going to a private stream."""
+    if stream is None:
+        return None
+    s = int(stream)
+    return CUDA_STREAM_LEGACY if s == 0 else s
+
+
+def _chk(rc: int, where: str, allow=()):
+    if rc != RDC_OK and rc not in allow:
+        raise RdcError(rc, where)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+
+def rdc_status_str(rc: int) -> str:
+    return lib().rdc_status_str(int(rc)).decode()
+
+
+def rdc_last_error() -> str:
+    return lib().rdc_last_error().decode()
+
+
+def rdc_params_default(**overrides) -> rdc_params:
+    p = rdc_params()
+    _chk(lib().rdc_params_default(ctypes.byref(p)), "rdc_params_default")
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION_NAMES[v]
+        setattr(p, k, v)
+    return p
+
+
+def rdc_create(width: int, height: int, params: rdc_params, phi=None, stream=None):
+    """Returns an opaque handle (int).  phi: H x W float32 (or float64, which
+    routes to rdc_create_f64phi) host array, or None for uniform phi_active."""
+    h = _P()
+    g = rdc_grid(int(width), int(height))
+    if phi is None:
+        rc = lib().rdc_create(g, ctypes.byref(params), None, _stream(stream), ctypes.byref(h))
+        _chk(rc, "rdc_create")
+        return h.value
+    ptr, code, shape = _host_ptr(phi, "phi")
+    if shape != (height, width):
+        raise ValueError(f"phi shape {shape} != ({height}, {width})")
+    if code == RDC_DTYPE_F32:
+        rc = lib().rdc_create(g, ctypes.byref(params), ptr, _stream(stream), ctypes.byref(h))
+    elif code == RDC_DTYPE_F64:
+        rc = lib().rdc_create_f64phi(g, ctypes.byref(params), ptr, _stream(stream), ctypes.byref(h))
+    else:
+        raise ValueError("phi must be float32 or float64")
+    _chk(rc, "rdc_create")
+    return h.value
+
+
+def rdc_create_f64phi(width: int, height: int, params: rdc_params, phi, stream=None):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    return rdc_create(width, height, params, phi, stream)
+
+
+def rdc_create_ext(width: int, height: int, params: rdc_params, dev_u, dev_v, dev_phi,
+                   pitch_bytes: int, stream=None):
+    """dev_u, dev_v: pairs of device pointers (ints); dev_phi a device pointer."""
+    h = _P()
+    U = (_P * 2)(*[int(x) for x in dev_u])
+    V = (_P * 2)(*[int(x) for x in dev_v])
+    rc = lib().rdc_create_ext(rdc_grid(int(width), int(height)), ctypes.byref(params), U, V,
+                              int(dev_phi), int(pitch_bytes), _stream(stream), ctypes.byref(h))
+    _chk(rc, "rdc_create_ext")
+    return h.value
+
+
+def rdc_destroy(h) -> None:
+    if h:
+        lib().rdc_destroy(h)
+
+
+def rdc_set_phi(h, phi) -> int:
+    ptr, code, _ = _host_ptr(phi, "phi")
+    return _chk(lib().rdc_set_phi(h, ptr, code), "rdc_set_phi")
+
+
+def rdc_reset_rest(h) -> int:
+    return _chk(lib().rdc_reset_rest(h), "rdc_reset_rest")
+
+
+def rdc_seed(h, cx: float, cy: float, r: float, value: float) -> int:
+    return _chk(lib().rdc_seed(h, float(cx), float(cy), float(r), float(value)), "rdc_seed")
+
+
+def rdc_set_state(h, u=None, v=None) -> int:
+    pu, cu, _ = _host_ptr(u, "u")
+    pv, cv, _ = _host_ptr(v, "v")
+    if cu is not None and cv is not None and cu != cv:
+        raise ValueError("u and v must have the same dtype")
+    code = cu if cu is not None else cv
+    if code is None:
+        return RDC_OK
+    return _chk(lib().rdc_set_state(h, pu, pv, code), "rdc_set_state")
+
+
+def rdc_step(h, n: int) -> int:
+    return _chk(lib().rdc_step(h, int(n)), "rdc_step")
+
+
+def rdc_read(h, u_out=None, v_out=None):
+    """Fills caller-owned host arrays (same dtype); returns the status
+    (RDC_OK or RDC_ENONFINITE)."""
+    pu, cu, _ = _host_ptr(u_out, "u_out")
+    pv, cv, _ = _host_ptr(v_out, "v_out")
+    if cu is not None and cv is not None and cu != cv:
+        raise ValueError("u_out and v_out must have the same dtype")
+    code = cu if cu is not None else (cv if cv is not None else RDC_DTYPE_F64)
+    return _chk(lib().rdc_read(h, pu, pv, code), "rdc_read", allow=(RDC_ENONFINITE,))
+
+
+def rdc_check(h):
+    """(status, first_bad_flat_index or -1)."""
+    fb = ctypes.c_int64(-1)
+    rc = _chk(lib().rdc_check(h, ctypes.byref(fb)), "rdc_check", allow=(RDC_ENONFINITE,))
+    return rc, fb.value
+
+
+def rdc_probe(h, cells) -> np.ndarray:
+    c = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.empty(len(c), dtype=np.float64)
+    _chk(lib().rdc_probe(h, len(c), c.ctypes.data, out.ctypes.data), "rdc_probe")
+    return out
+
+
+def rdc_sync(h) -> int:
+    return _chk(lib().rdc_sync(h), "rdc_sync")
+
+
+def rdc_rest_state(phi: float, f: float, q: float) -> float:
+    out = ctypes.c_double()
+    _chk(lib().rdc_rest_state(float(phi), float(f), float(q), ctypes.byref(out)), "rdc_rest_state")
+    return out.value
+
+
+def rdc_stability(h):
+    """(status, rho) with status RDC_OK or RDC_EUNSTABLE_WARN."""
+    rho = ctypes.c_double()
+    rc = _chk(lib().rdc_stability(h, ctypes.byref(rho)), "rdc_stability",
+              allow=(RDC_EUNSTABLE_WARN,))
+    return rc, rho.value
+
+
+def rdc_get_view(h) -> rdc_view:
+    v = rdc_view()
+    _chk(lib().rdc_get_view(h, ctypes.byref(v)), "rdc_get_view")
+    return v
+
+
+def rdc_get_shape(h) -> rdc_launch_shape:
+    s = rdc_launch_shape()
+    _chk(lib().rdc_get_shape(h, ctypes.byref(s)), "rdc_get_shape")
+    return s
+
+
+def rdc_set_shape(h, bx: int, rows: int, tx: int, ty: int, nthreads: int, k: int) -> int:
+    s = rdc_launch_shape(bx, rows, tx, ty, nthreads, k)
+    return _chk(lib().rdc_set_shape(h, ctypes.byref(s)), "rdc_set_shape")

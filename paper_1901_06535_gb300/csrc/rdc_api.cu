@@ -1,0 +1,664 @@
+// C ABI of librdc (include/rdc.h): handles, validation, memory layout,
+// dispatch of the step kernels, host <-> device transfers.
+//
+// Device layout of a library-owned simulation: one allocation holding
+//   u[0], u[1], v[0], v[1]  (storage type, ping-pong),  phi  (float, or
+//   double in FP64 mode),  then a small scratch area (health flag, probe
+//   buffers);
+// every plane is row-major with a row pitch of roundup(W, 64) elements, so
+// each row starts on a 128-byte boundary and 16-byte vector accesses of any
+// storage type stay aligned.  Plane offsets are multiples of 256 bytes.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rdc.h"
+#include "rdc_internal.h"
+
+namespace rdc {
+cudaError_t launch_step1_f32(int, const Planes&, const ModelD&, Shape1, cudaStream_t);
+cudaError_t launch_step1_f64(int, const Planes&, const ModelD&, Shape1, cudaStream_t);
+cudaError_t launch_step1_bf16(int, const Planes&, const ModelD&, Shape1, cudaStream_t);
+cudaError_t launch_step1_f16(int, const Planes&, const ModelD&, Shape1, cudaStream_t);
+cudaError_t launch_stepk_f32(int, const Planes&, const ModelD&, ShapeK, cudaStream_t);
+cudaError_t launch_stepk_f64(int, const Planes&, const ModelD&, ShapeK, cudaStream_t);
+cudaError_t launch_stepk_bf16(int, const Planes&, const ModelD&, ShapeK, cudaStream_t);
+cudaError_t launch_stepk_f16(int, const Planes&, const ModelD&, ShapeK, cudaStream_t);
+size_t stepk_smem_f32(ShapeK);
+size_t stepk_smem_f64(ShapeK);
+size_t stepk_smem_bf16(ShapeK);
+size_t stepk_smem_f16(ShapeK);
+cudaError_t launch_fill_phi(int prec, void* dst, int W, int H, int64_t pitch,
+                            double value, cudaStream_t st);
+
+cudaError_t launch_step1(int prec, int mode, const Planes& g, const ModelD& m,
+                         Shape1 s, cudaStream_t st)
+{
+    switch (prec) {
+        case P_F32: return launch_step1_f32(mode, g, m, s, st);
+        case P_F64: return launch_step1_f64(mode, g, m, s, st);
+        case P_BF16: return launch_step1_bf16(mode, g, m, s, st);
+        case P_F16: return launch_step1_f16(mode, g, m, s, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stepk(int prec, int mode, const Planes& g, const ModelD& m,
+                         ShapeK s, cudaStream_t st)
+{
+    switch (prec) {
+        case P_F32: return launch_stepk_f32(mode, g, m, s, st);
+        case P_F64: return launch_stepk_f64(mode, g, m, s, st);
+        case P_BF16: return launch_stepk_bf16(mode, g, m, s, st);
+        case P_F16: return launch_stepk_f16(mode, g, m, s, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t stepk_smem_bytes(int prec, ShapeK s)
+{
+    switch (prec) {
+        case P_F32: return stepk_smem_f32(s);
+        case P_F64: return stepk_smem_f64(s);
+        case P_BF16: return stepk_smem_bf16(s);
+        case P_F16: return stepk_smem_f16(s);
+    }
+    return 0;
+}
+}  // namespace rdc
+
+using namespace rdc;
+
+// Table 1 of the paper.
+static const double kEps = 0.0243, kF = 1.4, kQ = 0.002, kDu = 0.45,
+                    kDt = 0.001, kDx = 0.25, kPhiActive = 0.054;
+
+static const int kProbeChunk = 256;
+static const size_t kMiscBytes = 256 + kProbeChunk * 16;
+
+struct rdc_sim {
+    int W = 0, H = 0;
+    rdc_params p{};
+    int prec = 0, mode = 0;
+    int64_t pitch = 0;  // elements, all planes
+    void* base = nullptr;
+    bool owns = false;
+    void* u[2] = {nullptr, nullptr};
+    void* v[2] = {nullptr, nullptr};
+    void* phi = nullptr;
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    unsigned char* misc = nullptr;  // flag at +0, probe cells at +256, out after
+    bool owns_misc = false;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    int64_t steps_done = 0, launches = 0;
+    double phi_max = 0.0;
+    Shape1 shape1{128, 16};
+    ShapeK shapek{64, 32, 1, 256};
+};
+
+static thread_local char g_err[512] = "";
+
+static int cuda_fail(cudaError_t e, const char* what)
+{
+    std::snprintf(g_err, sizeof g_err, "%s: %s (%s)", what, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? RDC_ENOMEM : RDC_ECUDA;
+}
+
+#define CK(call, what)                               \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+static ModelD model_of(const rdc_params& p)
+{
+    ModelD m;
+    m.eps = p.eps;
+    m.f = p.f;
+    m.q = p.q;
+    m.Du = p.Du;
+    m.dt = p.dt;
+    m.inv_dx2 = 1.0 / (p.dx * p.dx);
+    return m;
+}
+
+static bool params_valid(const rdc_params* p)
+{
+    if (!p) return false;
+    const double vals[6] = {p->eps, p->f, p->q, p->Du, p->dt, p->dx};
+    for (double x : vals)
+        if (!std::isfinite(x)) return false;
+    if (!(p->eps > 0.0) || !(p->q > 0.0) || !(p->q < 1.0) || !(p->dt > 0.0) ||
+        !(p->dx > 0.0) || p->Du < 0.0)
+        return false;
+    if (!(p->f + p->q > 1.0)) return false;
+    if (p->Du * p->dt / (p->dx * p->dx) > 0.25) return false;
+    if (p->precision < 0 || p->precision > 3) return false;
+    if (p->flags < 0 || p->flags > 2) return false;
+    if (p->k_block < 0 || p->k_block > 8) return false;
+    if (p->reserved != 0) return false;
+    return true;
+}
+
+static bool phi_ok(double phi, const rdc_params* p)
+{
+    return std::isfinite(phi) && phi > p->q * (1.0 + p->f);
+}
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+static int check_device()
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    int major = 0, minor = 0;
+    CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev), "cudaDeviceGetAttribute");
+    CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev), "cudaDeviceGetAttribute");
+    if (major != 10 || minor != 3) {
+        std::snprintf(g_err, sizeof g_err,
+                      "librdc is built for sm_103a only; device %d is sm_%d%d",
+                      dev, major, minor);
+        return RDC_EUNSUPPORTED;
+    }
+    return RDC_OK;
+}
+
+static void default_shapes(rdc_sim* s)
+{
+    const int vec = vec_cells(s->prec);
+    const int64_t vecs = (s->W + vec - 1) / vec;
+    int bx = 128;
+    if (vecs < bx) bx = (int)std::max<int64_t>(32, round_up(vecs, 32));
+    const int64_t ncb = (vecs + bx - 1) / bx;
+    int rows = 32;
+    while (rows > 4 && ncb * ((s->H + rows - 1) / rows) < 152 * 8) rows /= 2;
+    s->shape1 = Shape1{bx, rows};
+    if (s->prec == P_F64)
+        s->shapek = ShapeK{32, 32, 1, 256};
+    else
+        s->shapek = ShapeK{64, 32, 1, 256};
+    s->shapek.k = s->p.k_block == 0 ? 1 : s->p.k_block;
+}
+
+static void destroy_impl(rdc_sim* s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->owns && s->base) cudaFree(s->base);
+    if (s->owns_misc && s->misc) cudaFree(s->misc);
+    if (s->stage) cudaFree(s->stage);
+    if (s->owns_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+static int ensure_stage(rdc_sim* s, size_t bytes)
+{
+    if (s->stage_bytes >= bytes) return RDC_OK;
+    if (s->stage) {
+        CK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+        cudaFree(s->stage);
+        s->stage = nullptr;
+        s->stage_bytes = 0;
+    }
+    CK(cudaMalloc(&s->stage, bytes), "cudaMalloc(stage)");
+    s->stage_bytes = bytes;
+    return RDC_OK;
+}
+
+// Host phi (float or double, packed) -> device phi plane.
+static int upload_phi(rdc_sim* s, const void* phi_host, int dtype)
+{
+    const int pb = phi_bytes(s->prec);
+    const bool direct = (dtype == 0 && pb == 4) || (dtype == 1 && pb == 8);
+    if (direct) {
+        CK(cudaMemcpy2DAsync(s->phi, (size_t)s->pitch * pb, phi_host, (size_t)s->W * pb,
+                             (size_t)s->W * pb, s->H, cudaMemcpyHostToDevice, s->stream),
+           "cudaMemcpy2DAsync(phi)");
+        return RDC_OK;
+    }
+    const size_t bytes = (size_t)s->W * s->H * dtype_bytes(dtype);
+    int rc = ensure_stage(s, bytes);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(s->stage, phi_host, bytes, cudaMemcpyHostToDevice, s->stream),
+       "cudaMemcpyAsync(phi)");
+    CK(launch_phi_in(s->prec, dtype, s->stage, s->phi, s->W, s->H, s->pitch, s->stream),
+       "phi conversion kernel");
+    return RDC_OK;
+}
+
+// Validates a host phi map and returns its maximum.
+static bool scan_phi(const void* phi_host, int dtype, int64_t n, const rdc_params* p,
+                     double* mx)
+{
+    double m = -INFINITY;
+    for (int64_t k = 0; k < n; ++k) {
+        const double x = dtype == 0 ? (double)((const float*)phi_host)[k]
+                                    : ((const double*)phi_host)[k];
+        if (!phi_ok(x, p)) return false;
+        if (x > m) m = x;
+    }
+    *mx = m;
+    return true;
+}
+
+static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
+                         int phi_dtype, void* stream, void* const* ext_u,
+                         void* const* ext_v, const void* ext_phi,
+                         size_t ext_pitch_bytes, rdc_sim** out)
+{
+    if (!out) return RDC_EINVAL;
+    *out = nullptr;
+    if (g.width < 1 || g.height < 1 || !params_valid(p)) return RDC_EINVAL;
+    const int64_t n = (int64_t)g.width * g.height;
+    double phi_max = kPhiActive;
+    if (phi_host) {
+        if (!scan_phi(phi_host, phi_dtype, n, p, &phi_max)) return RDC_EINVAL;
+    } else if (!ext_u && !phi_ok(kPhiActive, p)) {
+        return RDC_EINVAL;
+    }
+    const int prec = p->precision;
+    const int esz = state_bytes(prec);
+    if (ext_u) {
+        for (int b = 0; b < 2; ++b)
+            if (!ext_u[b] || !ext_v[b] || ((uintptr_t)ext_u[b] % 16) || ((uintptr_t)ext_v[b] % 16))
+                return RDC_EINVAL;
+        if (!ext_phi || ((uintptr_t)ext_phi % 16)) return RDC_EINVAL;
+        if (ext_pitch_bytes % 16 || ext_pitch_bytes < (size_t)g.width * esz ||
+            ext_pitch_bytes % esz)
+            return RDC_EINVAL;
+    }
+    int rc = check_device();
+    if (rc) return rc;
+
+    rdc_sim* s = new (std::nothrow) rdc_sim();
+    if (!s) return RDC_ENOMEM;
+    s->W = g.width;
+    s->H = g.height;
+    s->p = *p;
+    s->prec = prec;
+    s->mode = p->flags;
+    s->phi_max = phi_max;
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete s;
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        s->owns_stream = true;
+    }
+
+    if (ext_u) {
+        s->pitch = (int64_t)(ext_pitch_bytes / esz);
+        s->u[0] = ext_u[0];
+        s->u[1] = ext_u[1];
+        s->v[0] = ext_v[0];
+        s->v[1] = ext_v[1];
+        s->phi = const_cast<void*>(ext_phi);
+        cudaError_t e = cudaMalloc((void**)&s->misc, kMiscBytes);
+        if (e != cudaSuccess) {
+            destroy_impl(s);
+            return cuda_fail(e, "cudaMalloc(scratch)");
+        }
+        s->owns_misc = true;
+    } else {
+        s->pitch = round_up(g.width, 64);
+        const size_t sp = (size_t)round_up((int64_t)s->pitch * s->H * esz, 256);
+        const size_t pp = (size_t)round_up((int64_t)s->pitch * s->H * phi_bytes(prec), 256);
+        const size_t total = 4 * sp + pp + kMiscBytes;
+        cudaError_t e = cudaMalloc(&s->base, total);
+        if (e != cudaSuccess) {
+            destroy_impl(s);
+            return cuda_fail(e, "cudaMalloc(planes)");
+        }
+        s->owns = true;
+        unsigned char* b = (unsigned char*)s->base;
+        s->u[0] = b;
+        s->u[1] = b + sp;
+        s->v[0] = b + 2 * sp;
+        s->v[1] = b + 3 * sp;
+        s->phi = b + 4 * sp;
+        s->misc = b + 4 * sp + pp;
+        e = cudaMemsetAsync(s->base, 0, total, s->stream);
+        if (e != cudaSuccess) {
+            destroy_impl(s);
+            return cuda_fail(e, "cudaMemsetAsync");
+        }
+        if (phi_host) {
+            rc = upload_phi(s, phi_host, phi_dtype);
+        } else {
+            e = launch_fill_phi(prec, s->phi, s->W, s->H, s->pitch, kPhiActive, s->stream);
+            rc = e == cudaSuccess ? RDC_OK : cuda_fail(e, "phi fill kernel");
+        }
+        if (rc == RDC_OK) {
+            e = launch_rest(prec, s->u[0], s->v[0], s->phi, s->W, s->H, s->pitch, p->f,
+                            p->q, s->stream);
+            rc = e == cudaSuccess ? RDC_OK : cuda_fail(e, "rest-state kernel");
+        }
+        if (rc == RDC_OK) {
+            e = cudaStreamSynchronize(s->stream);
+            rc = e == cudaSuccess ? RDC_OK : cuda_fail(e, "cudaStreamSynchronize");
+        }
+        if (rc != RDC_OK) {
+            destroy_impl(s);
+            return rc;
+        }
+    }
+    default_shapes(s);
+    *out = s;
+    return RDC_OK;
+}
+
+extern "C" {
+
+int rdc_params_default(rdc_params* out)
+{
+    if (!out) return RDC_EINVAL;
+    std::memset(out, 0, sizeof *out);
+    out->eps = kEps;
+    out->f = kF;
+    out->q = kQ;
+    out->Du = kDu;
+    out->dt = kDt;
+    out->dx = kDx;
+    out->precision = RDC_F32;
+    out->flags = 0;
+    out->k_block = 0;
+    out->reserved = 0;
+    return RDC_OK;
+}
+
+int rdc_create(rdc_grid g, const rdc_params* p, const float* phi_host,
+               void* stream, rdc_sim** out)
+{
+    return create_common(g, p, phi_host, 0, stream, nullptr, nullptr, nullptr, 0, out);
+}
+
+int rdc_create_f64phi(rdc_grid g, const rdc_params* p, const double* phi_host,
+                      void* stream, rdc_sim** out)
+{
+    return create_common(g, p, phi_host, 1, stream, nullptr, nullptr, nullptr, 0, out);
+}
+
+int rdc_create_ext(rdc_grid g, const rdc_params* p, void* const dev_u[2],
+                   void* const dev_v[2], const void* dev_phi, size_t pitch_bytes,
+                   void* stream, rdc_sim** out)
+{
+    if (!dev_u || !dev_v) return RDC_EINVAL;
+    return create_common(g, p, nullptr, 0, stream, dev_u, dev_v, dev_phi, pitch_bytes, out);
+}
+
+void rdc_destroy(rdc_sim* sim) { destroy_impl(sim); }
+
+int rdc_reset_rest(rdc_sim* s)
+{
+    if (!s) return RDC_EINVAL;
+    CK(launch_rest(s->prec, s->u[0], s->v[0], s->phi, s->W, s->H, s->pitch, s->p.f,
+                   s->p.q, s->stream),
+       "rest-state kernel");
+    s->cur = 0;
+    s->steps_done = 0;
+    return RDC_OK;
+}
+
+int rdc_set_phi(rdc_sim* s, const void* phi_host, int32_t dtype)
+{
+    if (!s || !phi_host || (dtype != 0 && dtype != 1)) return RDC_EINVAL;
+    double mx = 0.0;
+    if (!scan_phi(phi_host, dtype, (int64_t)s->W * s->H, &s->p, &mx)) return RDC_EINVAL;
+    int rc = upload_phi(s, phi_host, dtype);
+    if (rc) return rc;
+    s->phi_max = mx;
+    return rdc_reset_rest(s);
+}
+
+int rdc_seed(rdc_sim* s, double cx, double cy, double r, double value)
+{
+    if (!s || !std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(value) ||
+        !(r >= 0.0) || !(r < 16777216.0))
+        return RDC_EINVAL;
+    CK(launch_seed(s->prec, s->u[s->cur], s->W, s->H, s->pitch, cx, cy, r, value, s->stream),
+       "seed kernel");
+    return RDC_OK;
+}
+
+int rdc_set_state(rdc_sim* s, const void* u_host, const void* v_host, int32_t dtype)
+{
+    if (!s || dtype < 0 || dtype > 3) return RDC_EINVAL;
+    const int esz = state_bytes(s->prec);
+    const void* src[2] = {u_host, v_host};
+    void* dst[2] = {s->u[s->cur], s->v[s->cur]};
+    for (int b = 0; b < 2; ++b) {
+        if (!src[b]) continue;
+        if (dtype == s->prec) {
+            CK(cudaMemcpy2DAsync(dst[b], (size_t)s->pitch * esz, src[b], (size_t)s->W * esz,
+                                 (size_t)s->W * esz, s->H, cudaMemcpyHostToDevice, s->stream),
+               "cudaMemcpy2DAsync(state)");
+        } else {
+            const size_t bytes = (size_t)s->W * s->H * dtype_bytes(dtype);
+            int rc = ensure_stage(s, bytes);
+            if (rc) return rc;
+            CK(cudaMemcpyAsync(s->stage, src[b], bytes, cudaMemcpyHostToDevice, s->stream),
+               "cudaMemcpyAsync(state)");
+            CK(launch_pack_in(s->prec, dtype, s->stage, dst[b], s->W, s->H, s->pitch, s->stream),
+               "state conversion kernel");
+        }
+    }
+    return RDC_OK;
+}
+
+int rdc_step(rdc_sim* s, int64_t n)
+{
+    if (!s || n < 0) return RDC_EINVAL;
+    const ModelD m = model_of(s->p);
+    int64_t left = n;
+    const int k = s->shapek.k;
+    while (left > 0) {
+        Planes g{s->u[s->cur], s->v[s->cur], s->phi, s->u[1 - s->cur], s->v[1 - s->cur],
+                 s->W, s->H, s->pitch};
+        cudaError_t e;
+        int done;
+        if (k > 1 && left >= k) {
+            e = launch_stepk(s->prec, s->mode, g, m, s->shapek, s->stream);
+            done = k;
+        } else {
+            e = launch_step1(s->prec, s->mode, g, m, s->shape1, s->stream);
+            done = 1;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+        s->cur = 1 - s->cur;
+        s->steps_done += done;
+        s->launches += 1;
+        left -= done;
+    }
+    return RDC_OK;
+}
+
+int rdc_check(rdc_sim* s, int64_t* first_bad)
+{
+    if (!s) return RDC_EINVAL;
+    unsigned long long* flag = (unsigned long long*)s->misc;
+    CK(cudaMemsetAsync(flag, 0xFF, sizeof(unsigned long long), s->stream), "cudaMemsetAsync(flag)");
+    CK(launch_health(s->prec, s->u[s->cur], s->W, s->H, s->pitch, s->p.q, flag, s->stream),
+       "health kernel");
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, s->stream), "cudaMemcpyAsync(flag)");
+    CK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    const bool bad = (h != ~0ull);
+    if (first_bad) *first_bad = bad ? (int64_t)h : -1;
+    return bad ? RDC_ENONFINITE : RDC_OK;
+}
+
+int rdc_read(rdc_sim* s, void* u_out, void* v_out, int32_t dtype)
+{
+    if (!s || dtype < 0 || dtype > 3) return RDC_EINVAL;
+    const int esz = state_bytes(s->prec);
+    const void* src[2] = {s->u[s->cur], s->v[s->cur]};
+    void* dst[2] = {u_out, v_out};
+    for (int b = 0; b < 2; ++b) {
+        if (!dst[b]) continue;
+        if (dtype == s->prec) {
+            CK(cudaMemcpy2DAsync(dst[b], (size_t)s->W * esz, src[b], (size_t)s->pitch * esz,
+                                 (size_t)s->W * esz, s->H, cudaMemcpyDeviceToHost, s->stream),
+               "cudaMemcpy2DAsync(read)");
+        } else {
+            const size_t bytes = (size_t)s->W * s->H * dtype_bytes(dtype);
+            int rc = ensure_stage(s, bytes);
+            if (rc) return rc;
+            CK(launch_pack_out(s->prec, dtype, src[b], s->stage, s->W, s->H, s->pitch, s->stream),
+               "state conversion kernel");
+            CK(cudaMemcpyAsync(dst[b], s->stage, bytes, cudaMemcpyDeviceToHost, s->stream),
+               "cudaMemcpyAsync(read)");
+            CK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+        }
+    }
+    return rdc_check(s, nullptr);
+}
+
+int rdc_probe(rdc_sim* s, int32_t n, const int64_t* cells, double* out)
+{
+    if (!s || n < 0 || (n > 0 && (!cells || !out))) return RDC_EINVAL;
+    const int64_t ncell = (int64_t)s->W * s->H;
+    for (int32_t k = 0; k < n; ++k)
+        if (cells[k] < 0 || cells[k] >= ncell) return RDC_EINVAL;
+    int64_t* d_cells = (int64_t*)(s->misc + 256);
+    double* d_out = (double*)(s->misc + 256 + kProbeChunk * 8);
+    for (int32_t k0 = 0; k0 < n; k0 += kProbeChunk) {
+        const int m = std::min<int32_t>(kProbeChunk, n - k0);
+        CK(cudaMemcpyAsync(d_cells, cells + k0, m * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           s->stream),
+           "cudaMemcpyAsync(probe)");
+        CK(launch_probe(s->prec, s->u[s->cur], s->W, s->pitch, d_cells, m, d_out, s->stream),
+           "probe kernel");
+        CK(cudaMemcpyAsync(out + k0, d_out, m * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+           "cudaMemcpyAsync(probe)");
+        CK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    }
+    return RDC_OK;
+}
+
+int rdc_sync(rdc_sim* s)
+{
+    if (!s) return RDC_EINVAL;
+    CK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    return RDC_OK;
+}
+
+int rdc_rest_state(double phi, double f, double q, double* u_star)
+{
+    if (!u_star || !(q > 0.0 && q < 1.0) || !(f + q > 1.0) || !std::isfinite(f) ||
+        !(phi > q * (1.0 + f)) || !std::isfinite(phi))
+        return RDC_EINVAL;
+    // Same rule as the device initialiser.  This translation unit's host code
+    // is compiled with -ffp-contract=off, so each operation rounds once.
+    const double a2 = (f + q) - 1.0;
+    const double a1 = (phi - q) - f * q;
+    const double a0 = -(phi * q);
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 2000; ++it) {
+        const double mid = lo + (hi - lo) * 0.5;
+        if (mid == lo || mid == hi) break;
+        const double pv = ((mid + a2) * mid + a1) * mid + a0;
+        if (pv < 0.0) lo = mid; else hi = mid;
+    }
+    *u_star = hi;
+    return RDC_OK;
+}
+
+int rdc_stability(rdc_sim* s, double* rho_out)
+{
+    if (!s || !rho_out) return RDC_EINVAL;
+    const rdc_params& p = s->p;
+    double us = 0.0;
+    if (rdc_rest_state(s->phi_max, p.f, p.q, &us) != RDC_OK) return RDC_EINVAL;
+    // Jacobian of Eq. 1's reaction part at u = v = u*:
+    //   dR/du = 1 - 2u - (f v + phi) 2q/(u+q)^2,  dR/dv = -f (u-q)/(u+q)
+    const double a = 1.0 - 2.0 * us - (p.f * us + s->phi_max) * 2.0 * p.q / ((us + p.q) * (us + p.q));
+    const double b = -p.f * (us - p.q) / (us + p.q);
+    const double lap_min = -8.0 * p.Du / (p.dx * p.dx);
+    double rho = 0.0;
+    for (int k = 0; k <= 64; ++k) {
+        const double shift = lap_min * k / 64.0;
+        // J = [[a/eps + shift, b/eps], [1, -1]]
+        const double j11 = a / p.eps + shift, j12 = b / p.eps, j21 = 1.0, j22 = -1.0;
+        const double tr = j11 + j22, det = j11 * j22 - j12 * j21;
+        const std::complex<double> disc = std::sqrt(std::complex<double>(tr * tr - 4.0 * det, 0.0));
+        const std::complex<double> l1 = 0.5 * (tr + disc), l2 = 0.5 * (tr - disc);
+        rho = std::max(rho, std::abs(1.0 + p.dt * l1));
+        rho = std::max(rho, std::abs(1.0 + p.dt * l2));
+    }
+    *rho_out = rho;
+    return rho > 1.0 ? RDC_EUNSTABLE_WARN : RDC_OK;
+}
+
+int rdc_get_view(rdc_sim* s, rdc_view* out)
+{
+    if (!s || !out) return RDC_EINVAL;
+    out->u = s->u[s->cur];
+    out->v = s->v[s->cur];
+    out->phi = s->phi;
+    out->pitch_bytes = (size_t)s->pitch * state_bytes(s->prec);
+    out->phi_pitch_bytes = (size_t)s->pitch * phi_bytes(s->prec);
+    out->width = s->W;
+    out->height = s->H;
+    out->precision = s->prec;
+    out->elem_bytes = state_bytes(s->prec);
+    out->steps_done = s->steps_done;
+    out->launches = s->launches;
+    out->stream = (void*)s->stream;
+    return RDC_OK;
+}
+
+int rdc_get_shape(rdc_sim* s, rdc_launch_shape* out)
+{
+    if (!s || !out) return RDC_EINVAL;
+    out->bx = s->shape1.bx;
+    out->rows = s->shape1.rows;
+    out->tx = s->shapek.tx;
+    out->ty = s->shapek.ty;
+    out->nthreads = s->shapek.nthreads;
+    out->k = s->shapek.k;
+    return RDC_OK;
+}
+
+int rdc_set_shape(rdc_sim* s, const rdc_launch_shape* in)
+{
+    if (!s || !in) return RDC_EINVAL;
+    if (in->bx < 32 || in->bx > 256 || in->bx % 32 || in->rows < 1) return RDC_EINVAL;
+    if (in->k < 1 || in->k > 8 || in->tx < 1 || in->ty < 1 || in->nthreads < 32 ||
+        in->nthreads > 512 || in->nthreads % 32)
+        return RDC_EINVAL;
+    ShapeK sk{in->tx, in->ty, in->k, in->nthreads};
+    if (in->k > 1 && stepk_smem_bytes(s->prec, sk) > 227 * 1024) return RDC_EINVAL;
+    if (in->k > 1 && (s->H + in->ty - 1) / in->ty > 65535) return RDC_EINVAL;
+    s->shape1 = Shape1{in->bx, in->rows};
+    s->shapek = sk;
+    return RDC_OK;
+}
+
+const char* rdc_status_str(int status)
+{
+    switch (status) {
+        case RDC_OK: return "RDC_OK";
+        case RDC_EINVAL: return "RDC_EINVAL: invalid argument";
+        case RDC_ENOMEM: return "RDC_ENOMEM: allocation failed";
+        case RDC_ECUDA: return "RDC_ECUDA: CUDA call failed";
+        case RDC_ENONFINITE: return "RDC_ENONFINITE: non-finite u or u + q <= 0";
+        case RDC_ETIMEOUT: return "RDC_ETIMEOUT: bounded device wait gave up";
+        case RDC_EUNSTABLE_WARN: return "RDC_EUNSTABLE_WARN: forward Euler unstable at rest";
+        case RDC_EUNSUPPORTED: return "RDC_EUNSUPPORTED: not supported by this build or device";
+    }
+    return "unknown rdc status";
+}
+
+const char* rdc_last_error(void) { return g_err; }
+
+}  // extern "C"

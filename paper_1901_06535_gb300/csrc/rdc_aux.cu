@@ -1,0 +1,347 @@
+// Auxiliary kernels of librdc: rest-state initialisation, catalytic
+// stimulation (§2), the health flag, dtype conversion between packed host
+// order and the pitched device planes, and probe gathers.
+#include "rdc_device.cuh"
+#include "rdc_internal.h"
+
+namespace rdc {
+
+// ---------------------------------------------------------------------------
+// conversions by host dtype code (RDC_DTYPE_F32/F64/BF16/F16)
+// ---------------------------------------------------------------------------
+
+template <typename D>
+__device__ __forceinline__ D cvt_from_double(double x);
+template <>
+__device__ __forceinline__ float cvt_from_double<float>(double x) { return __double2float_rn(x); }
+template <>
+__device__ __forceinline__ double cvt_from_double<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_from_double<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+template <>
+__device__ __forceinline__ __half cvt_from_double<__half>(double x) { return __double2half(x); }
+
+__device__ __forceinline__ double to_double(float x) { return (double)x; }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+__device__ __forceinline__ double to_double(__half x) { return (double)__half2float(x); }
+
+// Direct single-rounding conversion Src -> Dst (every narrower value is
+// exactly representable in double, so going through double rounds once).
+template <typename Dst, typename Src>
+__device__ __forceinline__ Dst convert(Src x)
+{
+    return cvt_from_double<Dst>(to_double(x));
+}
+
+// ---------------------------------------------------------------------------
+// rest state
+// ---------------------------------------------------------------------------
+
+// Positive root of p(u) = u^3 + (f+q-1) u^2 + (phi-q-fq) u - phi q (Eq. 1's
+// reaction bracket with v = u, times u + q) by the bisection rule documented
+// at rdc_rest_state: FP64, one rounding per operation, no contraction.
+__device__ __forceinline__ double rest_root(double phi, double f, double q)
+{
+    const double a2 = __dsub_rn(__dadd_rn(f, q), 1.0);
+    const double a1 = __dsub_rn(__dsub_rn(phi, q), __dmul_rn(f, q));
+    const double a0 = -__dmul_rn(phi, q);
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 2000; ++it) {
+        const double mid = __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), 0.5));
+        if (mid == lo || mid == hi) break;
+        const double p = __dadd_rn(
+            __dmul_rn(__dadd_rn(__dmul_rn(__dadd_rn(mid, a2), mid), a1), mid), a0);
+        if (p < 0.0) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+template <typename S>
+__global__ void k_rest(S* __restrict__ u, S* __restrict__ v,
+                       const typename Traits<S>::PhiT* __restrict__ phi, int W,
+                       int H, int64_t pitch, double f, double q)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        const int64_t o = i * pitch + j;
+        const double r = rest_root((double)phi[o], f, q);
+        const S s = cvt_from_double<S>(r);
+        u[o] = s;
+        v[o] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stimulation (§2): u := value inside a disk
+// ---------------------------------------------------------------------------
+
+template <typename S>
+__global__ void k_seed(S* __restrict__ u, int W, int H, int64_t pitch,
+                       int i0, int j0, int ni, int nj, double cx, double cy,
+                       double r2, S value)
+{
+    const int64_t n = (int64_t)ni * nj;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = i0 + (int)(k / nj);
+        const int j = j0 + (int)(k % nj);
+        const double dy = __dsub_rn((double)i, cy);
+        const double dx = __dsub_rn((double)j, cx);
+        if (__dadd_rn(__dmul_rn(dy, dy), __dmul_rn(dx, dx)) <= r2)
+            u[(int64_t)i * pitch + j] = value;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// health flag
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool bad_cell(float x, float q) { return !isfinite(x) || !(__fadd_rn(x, q) > 0.0f); }
+__device__ __forceinline__ bool bad_cell(double x, double q) { return !isfinite(x) || !(__dadd_rn(x, q) > 0.0); }
+
+template <typename S>
+__global__ void k_health(const S* __restrict__ u, int W, int H, int64_t pitch,
+                         typename Traits<S>::T q, unsigned long long* first_bad)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        if (bad_cell(widen(u[i * pitch + j]), q))
+            atomicMin(first_bad, (unsigned long long)k);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// packed <-> pitched conversion
+// ---------------------------------------------------------------------------
+
+template <typename Src, typename Dst>
+__global__ void k_pack_in(const Src* __restrict__ src, Dst* __restrict__ dst,
+                          int W, int H, int64_t pitch)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        dst[i * pitch + j] = convert<Dst>(src[k]);
+    }
+}
+
+template <typename Src, typename Dst>
+__global__ void k_pack_out(const Src* __restrict__ src, Dst* __restrict__ dst,
+                           int W, int H, int64_t pitch)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        dst[k] = convert<Dst>(src[i * pitch + j]);
+    }
+}
+
+template <typename S>
+__global__ void k_probe(const S* __restrict__ u, int W, int64_t pitch,
+                        const int64_t* __restrict__ cells, int n,
+                        double* __restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        const int64_t c = cells[k];
+        const int64_t i = c / W, j = c - i * W;
+        out[k] = to_double(u[i * pitch + j]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static int grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 32) b = 152 * 32;  // grid-stride beyond 32 CTAs per SM
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_rest(int prec, void* u, void* v, const void* phi, int W,
+                        int H, int64_t pitch, double f, double q,
+                        cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    switch (prec) {
+        case P_F32: k_rest<float><<<b, t, 0, st>>>((float*)u, (float*)v, (const float*)phi, W, H, pitch, f, q); break;
+        case P_F64: k_rest<double><<<b, t, 0, st>>>((double*)u, (double*)v, (const double*)phi, W, H, pitch, f, q); break;
+        case P_BF16: k_rest<__nv_bfloat16><<<b, t, 0, st>>>((__nv_bfloat16*)u, (__nv_bfloat16*)v, (const float*)phi, W, H, pitch, f, q); break;
+        case P_F16: k_rest<__half><<<b, t, 0, st>>>((__half*)u, (__half*)v, (const float*)phi, W, H, pitch, f, q); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed(int prec, void* u, int W, int H, int64_t pitch,
+                        double cx, double cy, double r, double value,
+                        cudaStream_t st)
+{
+    // bounding box of the disk, clipped to the grid (all in FP64; the box is
+    // one cell wider than needed on each side, the kernel decides membership)
+    double lo_i = floor(cy - r) - 1.0, hi_i = ceil(cy + r) + 1.0;
+    double lo_j = floor(cx - r) - 1.0, hi_j = ceil(cx + r) + 1.0;
+    if (lo_i < 0.0) lo_i = 0.0;
+    if (lo_j < 0.0) lo_j = 0.0;
+    if (hi_i > H - 1) hi_i = H - 1;
+    if (hi_j > W - 1) hi_j = W - 1;
+    if (hi_i < lo_i || hi_j < lo_j) return cudaSuccess;  // disk misses the grid
+    const int i0 = (int)lo_i, j0 = (int)lo_j;
+    const int ni = (int)hi_i - i0 + 1, nj = (int)hi_j - j0 + 1;
+    const double r2 = r * r;
+    const int t = 256;
+    const int b = grid_for((int64_t)ni * nj, t);
+    switch (prec) {
+        case P_F32: k_seed<float><<<b, t, 0, st>>>((float*)u, W, H, pitch, i0, j0, ni, nj, cx, cy, r2, (float)value); break;
+        case P_F64: k_seed<double><<<b, t, 0, st>>>((double*)u, W, H, pitch, i0, j0, ni, nj, cx, cy, r2, value); break;
+        case P_BF16: k_seed<__nv_bfloat16><<<b, t, 0, st>>>((__nv_bfloat16*)u, W, H, pitch, i0, j0, ni, nj, cx, cy, r2, __double2bfloat16(value)); break;
+        case P_F16: k_seed<__half><<<b, t, 0, st>>>((__half*)u, W, H, pitch, i0, j0, ni, nj, cx, cy, r2, __double2half(value)); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_health(int prec, const void* u, int W, int H, int64_t pitch,
+                          double q, unsigned long long* first_bad,
+                          cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    switch (prec) {
+        case P_F32: k_health<float><<<b, t, 0, st>>>((const float*)u, W, H, pitch, (float)q, first_bad); break;
+        case P_F64: k_health<double><<<b, t, 0, st>>>((const double*)u, W, H, pitch, q, first_bad); break;
+        case P_BF16: k_health<__nv_bfloat16><<<b, t, 0, st>>>((const __nv_bfloat16*)u, W, H, pitch, (float)q, first_bad); break;
+        case P_F16: k_health<__half><<<b, t, 0, st>>>((const __half*)u, W, H, pitch, (float)q, first_bad); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename Src>
+static cudaError_t pack_in_src(int prec, const void* src, void* dst, int W, int H,
+                               int64_t pitch, int b, int t, cudaStream_t st)
+{
+    const Src* s = (const Src*)src;
+    switch (prec) {
+        case P_F32: k_pack_in<Src, float><<<b, t, 0, st>>>(s, (float*)dst, W, H, pitch); break;
+        case P_F64: k_pack_in<Src, double><<<b, t, 0, st>>>(s, (double*)dst, W, H, pitch); break;
+        case P_BF16: k_pack_in<Src, __nv_bfloat16><<<b, t, 0, st>>>(s, (__nv_bfloat16*)dst, W, H, pitch); break;
+        case P_F16: k_pack_in<Src, __half><<<b, t, 0, st>>>(s, (__half*)dst, W, H, pitch); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_in(int prec, int src_dtype, const void* src, void* dst,
+                           int W, int H, int64_t pitch, cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    switch (src_dtype) {
+        case 0: return pack_in_src<float>(prec, src, dst, W, H, pitch, b, t, st);
+        case 1: return pack_in_src<double>(prec, src, dst, W, H, pitch, b, t, st);
+        case 2: return pack_in_src<__nv_bfloat16>(prec, src, dst, W, H, pitch, b, t, st);
+        case 3: return pack_in_src<__half>(prec, src, dst, W, H, pitch, b, t, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename S>
+static cudaError_t pack_out_src(int dst_dtype, const void* src, void* dst, int W,
+                                int H, int64_t pitch, int b, int t, cudaStream_t st)
+{
+    const S* s = (const S*)src;
+    switch (dst_dtype) {
+        case 0: k_pack_out<S, float><<<b, t, 0, st>>>(s, (float*)dst, W, H, pitch); break;
+        case 1: k_pack_out<S, double><<<b, t, 0, st>>>(s, (double*)dst, W, H, pitch); break;
+        case 2: k_pack_out<S, __nv_bfloat16><<<b, t, 0, st>>>(s, (__nv_bfloat16*)dst, W, H, pitch); break;
+        case 3: k_pack_out<S, __half><<<b, t, 0, st>>>(s, (__half*)dst, W, H, pitch); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_out(int prec, int dst_dtype, const void* src, void* dst,
+                            int W, int H, int64_t pitch, cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    switch (prec) {
+        case P_F32: return pack_out_src<float>(dst_dtype, src, dst, W, H, pitch, b, t, st);
+        case P_F64: return pack_out_src<double>(dst_dtype, src, dst, W, H, pitch, b, t, st);
+        case P_BF16: return pack_out_src<__nv_bfloat16>(dst_dtype, src, dst, W, H, pitch, b, t, st);
+        case P_F16: return pack_out_src<__half>(dst_dtype, src, dst, W, H, pitch, b, t, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_phi_in(int prec, int src_dtype, const void* src, void* dst,
+                          int W, int H, int64_t pitch, cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    const bool dbl = (prec == P_F64);
+    if (src_dtype == 0) {
+        if (dbl) k_pack_in<float, double><<<b, t, 0, st>>>((const float*)src, (double*)dst, W, H, pitch);
+        else k_pack_in<float, float><<<b, t, 0, st>>>((const float*)src, (float*)dst, W, H, pitch);
+    } else if (src_dtype == 1) {
+        if (dbl) k_pack_in<double, double><<<b, t, 0, st>>>((const double*)src, (double*)dst, W, H, pitch);
+        else k_pack_in<double, float><<<b, t, 0, st>>>((const double*)src, (float*)dst, W, H, pitch);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename P>
+__global__ void k_fill(P* __restrict__ dst, int W, int H, int64_t pitch, P value)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        dst[i * pitch + j] = value;
+    }
+}
+
+cudaError_t launch_fill_phi(int prec, void* dst, int W, int H, int64_t pitch,
+                            double value, cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    if (prec == P_F64)
+        k_fill<double><<<b, t, 0, st>>>((double*)dst, W, H, pitch, value);
+    else
+        k_fill<float><<<b, t, 0, st>>>((float*)dst, W, H, pitch, (float)value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probe(int prec, const void* u, int W, int64_t pitch,
+                         const int64_t* cells, int n, double* out,
+                         cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int t = 128;
+    const int b = (n + t - 1) / t;
+    switch (prec) {
+        case P_F32: k_probe<float><<<b, t, 0, st>>>((const float*)u, W, pitch, cells, n, out); break;
+        case P_F64: k_probe<double><<<b, t, 0, st>>>((const double*)u, W, pitch, cells, n, out); break;
+        case P_BF16: k_probe<__nv_bfloat16><<<b, t, 0, st>>>((const __nv_bfloat16*)u, W, pitch, cells, n, out); break;
+        case P_F16: k_probe<__half><<<b, t, 0, st>>>((const __half*)u, W, pitch, cells, n, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rdc

@@ -1,0 +1,288 @@
+// Step kernels of the Oregonator model (Eq. 1, explicit Euler, five-node
+// Laplacian with zero-flux borders, §2).  Included once per storage type by
+// rdc_step_<type>.cu so the precisions compile in parallel.
+//
+//  k_step1 : one Euler step per launch.  HBM-bound: per cell it reads u, v,
+//            phi once and writes u', v' once.  Each thread owns one 16-byte
+//            vector of cells in a row and marches down `rows` rows, keeping
+//            the north / centre / south rows of u in registers, so u is read
+//            from memory once; east/west neighbours across vector edges come
+//            from warp shuffles, and only the two cells beyond each warp's
+//            span are loaded separately.
+//  k_stepk : k Euler steps per launch (temporal blocking).  A CTA loads a
+//            (tx + 2k) x (ty + 2k) tile of u, v, phi into shared memory and
+//            steps it k times, the valid region shrinking by one cell per
+//            side per step (ghost-zone recompute), then writes the tx x ty
+//            interior.  Each intermediate u, v is rounded to the storage type
+//            exactly as k_step1 stores it, so k launches of k_step1 and one
+//            launch of k_stepk give the same bits.
+#pragma once
+
+#include "rdc_device.cuh"
+#include "rdc_internal.h"
+
+namespace rdc {
+
+template <typename S, int MODE>
+__global__ void __launch_bounds__(256)
+k_step1(const S* __restrict__ u, const S* __restrict__ v,
+        const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
+        S* __restrict__ v1, int W, int H, int64_t pitch, int rows,
+        Model<typename Traits<S>::T> m)
+{
+    using T = typename Traits<S>::T;
+    constexpr int VEC = Traits<S>::VEC;
+    const int lane = threadIdx.x & 31;
+    const int col0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    const int row0 = blockIdx.y * rows;
+    const int row1 = min(row0 + rows, H);
+    const bool act = col0 < W;
+
+    T un[VEC], uc[VEC], us[VEC], vv[VEC], ph[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) un[e] = uc[e] = us[e] = vv[e] = ph[e] = T(0);
+
+    if (act) {
+        Vec<S>::load(u + (int64_t)max(row0 - 1, 0) * pitch + col0, un);
+        Vec<S>::load(u + (int64_t)row0 * pitch + col0, uc);
+    }
+    for (int r = row0; r < row1; ++r) {
+        const int64_t ro = (int64_t)r * pitch;
+        const int64_t rso = (int64_t)min(r + 1, H - 1) * pitch;
+        T wl = T(0), er = T(0);
+        if (act) {
+            Vec<S>::load(u + rso + col0, us);
+            Vec<S>::load_stream(v + ro + col0, vv);
+            load_phi<VEC>(phi + ro + col0, ph);
+            if (lane == 0) wl = (col0 > 0) ? widen(u[ro + col0 - 1]) : uc[0];
+            if (lane == 31 && col0 + VEC < W) er = widen(u[ro + col0 + VEC]);
+        }
+        const T wsh = __shfl_up_sync(0xffffffffu, uc[VEC - 1], 1);
+        const T esh = __shfl_down_sync(0xffffffffu, uc[0], 1);
+        if (lane != 0) wl = wsh;
+        if (lane != 31) er = esh;
+        if (act) {
+            T ou[VEC], ov[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const T w = (e == 0) ? wl : uc[e - 1];
+                T ea = (e == VEC - 1) ? er : uc[e + 1];
+                if (col0 + e >= W - 1) ea = uc[e];  // mirror at the east border
+                cell_update<MODE>(uc[e], w, ea, un[e], us[e], vv[e], ph[e], m, ou[e], ov[e]);
+            }
+            if (col0 + VEC <= W) {
+                Vec<S>::store(u1 + ro + col0, ou);
+                Vec<S>::store(v1 + ro + col0, ov);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    if (col0 + e < W) {
+                        u1[ro + col0 + e] = narrow<S>(ou[e]);
+                        v1[ro + col0 + e] = narrow<S>(ov[e]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            un[e] = uc[e];
+            uc[e] = us[e];
+        }
+    }
+}
+
+// Shared-memory layout of k_stepk: four planes of (tx+2k) x (ty+2k) compute
+// values: u (ping), u (pong), v (updated in place: v' of a cell depends only
+// on that cell), phi.
+template <typename S, int MODE>
+__global__ void __launch_bounds__(512)
+k_stepk(const S* __restrict__ u, const S* __restrict__ v,
+        const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
+        S* __restrict__ v1, int W, int H, int64_t pitch, int TX, int TY, int K,
+        Model<typename Traits<S>::T> m)
+{
+    using T = typename Traits<S>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int RX = TX + 2 * K, RY = TY + 2 * K;
+    const int area = RX * RY;
+    T* ua = reinterpret_cast<T*>(smem_raw);
+    T* ub = ua + area;
+    T* vs = ub + area;
+    T* ps = vs + area;
+
+    const int gx0 = blockIdx.x * TX - K;  // global column of local column 0
+    const int gy0 = blockIdx.y * TY - K;  // global row of local row 0
+    const int nt = blockDim.x;
+    const int tid = threadIdx.x;
+
+    // load the tile (cells outside the grid are never read)
+    for (int idx = tid; idx < area; idx += nt) {
+        const int ly = idx / RX, lx = idx - ly * RX;
+        const int gy = gy0 + ly, gx = gx0 + lx;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            const int64_t o = (int64_t)gy * pitch + gx;
+            ua[idx] = widen(u[o]);
+            vs[idx] = widen(v[o]);
+            ps[idx] = (T)phi[o];
+        }
+    }
+    __syncthreads();
+
+    const int lane = tid & 31, wy = tid >> 5, nwy = nt >> 5;
+    T* cur = ua;
+    T* nxt = ub;
+    for (int s = 1; s <= K; ++s) {
+        const int ylo = max(s, -gy0), yhi = min(RY - s, H - gy0);
+        const int xlo = max(s, -gx0), xhi = min(RX - s, W - gx0);
+        for (int ly = ylo + wy; ly < yhi; ly += nwy) {
+            const int gy = gy0 + ly;
+            const int rowo = ly * RX;
+            const int no = (gy > 0) ? -RX : 0;
+            const int so = (gy < H - 1) ? RX : 0;
+            for (int lx = xlo + lane; lx < xhi; lx += 32) {
+                const int gx = gx0 + lx;
+                const int i = rowo + lx;
+                const T c = cur[i];
+                const T w = (gx > 0) ? cur[i - 1] : c;
+                const T e = (gx < W - 1) ? cur[i + 1] : c;
+                const T n = cur[i + no];
+                const T so_v = cur[i + so];
+                T un, vn;
+                cell_update<MODE>(c, w, e, n, so_v, vs[i], ps[i], m, un, vn);
+                nxt[i] = quantize<S>(un);
+                vs[i] = quantize<S>(vn);
+            }
+        }
+        __syncthreads();
+        T* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+
+    // write the interior
+    for (int idx = tid; idx < TX * TY; idx += nt) {
+        const int iy = idx / TX, ix = idx - iy * TX;
+        const int gy = gy0 + K + iy, gx = gx0 + K + ix;
+        if (gy < H && gx < W) {
+            const int i = (iy + K) * RX + (ix + K);
+            const int64_t o = (int64_t)gy * pitch + gx;
+            u1[o] = narrow<S>(cur[i]);
+            v1[o] = narrow<S>(vs[i]);
+        }
+    }
+}
+
+template <typename S>
+Model<typename Traits<S>::T> make_model(const ModelD& d)
+{
+    using T = typename Traits<S>::T;
+    Model<T> m;
+    m.eps = (T)d.eps;
+    m.f = (T)d.f;
+    m.q = (T)d.q;
+    m.Du = (T)d.Du;
+    m.dt = (T)d.dt;
+    m.inv_dx2 = (T)d.inv_dx2;
+    return m;
+}
+
+template <typename S>
+cudaError_t launch_step1_t(int mode, const Planes& g, const ModelD& md, Shape1 sh,
+                           cudaStream_t st)
+{
+    using PhiT = typename Traits<S>::PhiT;
+    constexpr int VEC = Traits<S>::VEC;
+    if (sh.bx < 32 || sh.bx > 256 || (sh.bx % 32) != 0 || sh.rows < 1)
+        return cudaErrorInvalidValue;
+    const int vecs = (g.W + VEC - 1) / VEC;
+    int rows = sh.rows;
+    if ((g.H + rows - 1) / rows > 65535) rows = (g.H + 65534) / 65535;
+    dim3 grid((vecs + sh.bx - 1) / sh.bx, (g.H + rows - 1) / rows);
+    auto m = make_model<S>(md);
+    const S* u = static_cast<const S*>(g.u);
+    const S* v = static_cast<const S*>(g.v);
+    const PhiT* phi = static_cast<const PhiT*>(g.phi);
+    S* u1 = static_cast<S*>(g.u1);
+    S* v1 = static_cast<S*>(g.v1);
+    switch (mode) {
+        case MODE_FULL:
+            k_step1<S, MODE_FULL><<<grid, sh.bx, 0, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, rows, m);
+            break;
+        case MODE_DIFFUSION:
+            k_step1<S, MODE_DIFFUSION><<<grid, sh.bx, 0, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, rows, m);
+            break;
+        case MODE_REACTION:
+            k_step1<S, MODE_REACTION><<<grid, sh.bx, 0, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, rows, m);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+size_t stepk_smem_t(ShapeK s)
+{
+    using T = typename Traits<S>::T;
+    return (size_t)4 * (s.tx + 2 * s.k) * (s.ty + 2 * s.k) * sizeof(T);
+}
+
+template <typename S, int MODE>
+cudaError_t set_stepk_attr(size_t smem)
+{
+    // Largest dynamic shared memory already granted, per device, per
+    // instantiation; raised monotonically.
+    static size_t configured[64] = {0};
+    if (smem <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (smem > configured[dev]) {
+        e = cudaFuncSetAttribute(k_stepk<S, MODE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = smem;
+    }
+    return cudaSuccess;
+}
+
+template <typename S>
+cudaError_t launch_stepk_t(int mode, const Planes& g, const ModelD& md, ShapeK sh,
+                           cudaStream_t st)
+{
+    using PhiT = typename Traits<S>::PhiT;
+    if (sh.k < 1 || sh.k > 8 || sh.tx < 1 || sh.ty < 1 || sh.nthreads < 32 ||
+        sh.nthreads > 512 || (sh.nthreads % 32) != 0)
+        return cudaErrorInvalidValue;
+    const size_t smem = stepk_smem_t<S>(sh);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    dim3 grid((g.W + sh.tx - 1) / sh.tx, (g.H + sh.ty - 1) / sh.ty);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    auto m = make_model<S>(md);
+    const S* u = static_cast<const S*>(g.u);
+    const S* v = static_cast<const S*>(g.v);
+    const PhiT* phi = static_cast<const PhiT*>(g.phi);
+    S* u1 = static_cast<S*>(g.u1);
+    S* v1 = static_cast<S*>(g.v1);
+    cudaError_t e;
+    switch (mode) {
+        case MODE_FULL:
+            if ((e = set_stepk_attr<S, MODE_FULL>(smem)) != cudaSuccess) return e;
+            k_stepk<S, MODE_FULL><<<grid, sh.nthreads, smem, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, sh.tx, sh.ty, sh.k, m);
+            break;
+        case MODE_DIFFUSION:
+            if ((e = set_stepk_attr<S, MODE_DIFFUSION>(smem)) != cudaSuccess) return e;
+            k_stepk<S, MODE_DIFFUSION><<<grid, sh.nthreads, smem, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, sh.tx, sh.ty, sh.k, m);
+            break;
+        case MODE_REACTION:
+            if ((e = set_stepk_attr<S, MODE_REACTION>(smem)) != cudaSuccess) return e;
+            k_stepk<S, MODE_REACTION><<<grid, sh.nthreads, smem, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, sh.tx, sh.ty, sh.k, m);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rdc

@@ -159,18 +159,20 @@ def and_gate(W: int = 256, H: int = 256, *, channel: float = 16.0,
 
 
 # Calibrated on the oracle (tests/golden/diode_calibration.txt): with a
-# 24-cell channel and a 1-cell gap of Table 1's phi_passive, points of 8 to
-# 12 cells all pass anode -> cathode and block cathode -> anode.
+# 24-cell channel and a 1-cell gap, gap levels phi in [0.11, 0.115] with
+# points of 4 to 10 cells all pass anode -> cathode and block cathode ->
+# anode; (0.11, 8) has a working neighbour on every side.
 DIODE_GAP_CELLS = 1
-DIODE_TIP_CELLS = 10.0
+DIODE_TIP_CELLS = 8.0
 DIODE_CHANNEL = 24.0
+DIODE_PHI_GAP = 0.11
 
 
 def diode(W: int = 128, H: int = 48, *, channel: float = DIODE_CHANNEL,
           gap: float = DIODE_GAP_CELLS, tip: float = DIODE_TIP_CELLS,
           phi_active: float = PHI_ACTIVE,
           phi_passive: float = PHI_PASSIVE_STRONG,
-          phi_gap: float | None = PHI_PASSIVE_PAPER,
+          phi_gap: float | None = DIODE_PHI_GAP,
           seed_r: float = 6.0, flip: bool = False) -> Circuit:
     """Chemical diode (§4.2).
 
@@ -178,8 +180,8 @@ def diode(W: int = 128, H: int = 48, *, channel: float = DIODE_CHANNEL,
     The anode side ends flat at the gap; the cathode side ends in a triangle
     whose point (``tip`` cells long) faces the gap.  Inside the channel's
     bounding box the non-active cells (the gap and the flanks of the point)
-    hold ``phi_gap`` (default: Table 1's phi_passive); everything else is
-    ``phi_passive``.  By the paper's account a
+    hold ``phi_gap`` (a weaker inhibitor than the background); everything
+    else is ``phi_passive``.  By the paper's account a
     wave passes from anode to cathode but not from cathode to anode.  The
     anode is on the left (``flip`` mirrors the map left-right).  Seeds sit at
     the two far ends; probes sit near each end, past the gap.

@@ -1,0 +1,81 @@
+"""The C-ABI library without a GPU: it loads, exports every function that
+include/rdc.h declares, validates arguments, and its host-side rest-state
+root equals the oracle's bit for bit.  No kernel is launched."""
+from __future__ import annotations
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tests import oracle_pins as P
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "rdc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(rdc_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(librdc):
+    names = declared_functions()
+    assert len(names) >= 20, names
+    lib = librdc.lib()
+    for n in names:
+        assert hasattr(lib, n), f"librdc.so does not export {n}"
+    from paper_1901_06535_gb300 import _capi
+    assert set(names) <= set(_capi.exported_symbols()) | set(names)
+    missing = set(names) - set(_capi.exported_symbols())
+    assert not missing, f"binding lacks {missing}"
+
+
+def test_params_default_is_table1(librdc):
+    p = librdc.rdc_params_default()
+    assert (p.eps, p.f, p.q, p.Du, p.dt, p.dx) == (P.EPS, P.F, P.Q, P.DU, P.DT, P.DX)
+    assert p.precision == 0 and p.flags == 0 and p.k_block == 0 and p.reserved == 0
+
+
+@pytest.mark.parametrize("phi", [0.054, 0.0975, 0.2, 0.05, 0.08, 0.0301, 0.5])
+def test_host_rest_state_bitwise_vs_oracle(librdc, orc, phi):
+    assert librdc.rdc_rest_state(phi, P.F, P.Q) == orc.rest_state(phi)
+
+
+def test_rest_state_rejects_no_root(librdc):
+    with pytest.raises(librdc.RdcError):
+        librdc.rdc_rest_state(0.001, P.F, P.Q)      # phi <= q (1 + f)
+    with pytest.raises(librdc.RdcError):
+        librdc.rdc_rest_state(0.054, 0.5, P.Q)      # f + q <= 1
+
+
+@pytest.mark.parametrize("bad", [dict(eps=0.0), dict(q=-1.0), dict(dt=float("nan")),
+                                 dict(Du=-0.1), dict(dx=0.0), dict(dt=0.05),
+                                 dict(flags=3), dict(precision=7), dict(k_block=9),
+                                 dict(reserved=1), dict(f=0.5)])
+def test_create_validates_params_before_touching_the_device(librdc, bad):
+    p = librdc.rdc_params_default(**bad)
+    with pytest.raises(librdc.RdcError) as e:
+        librdc.rdc_create(16, 16, p)
+    assert e.value.status == librdc.RDC_EINVAL
+
+
+def test_create_validates_grid_and_phi(librdc):
+    p = librdc.rdc_params_default()
+    for W, H in ((0, 5), (5, 0), (-1, 3)):
+        with pytest.raises(librdc.RdcError) as e:
+            librdc.rdc_create(W, H, p)
+        assert e.value.status == librdc.RDC_EINVAL
+    for bad in (np.nan, 0.001, np.inf):
+        phi = np.full((4, 4), 0.054, dtype=np.float32)
+        phi[2, 1] = bad
+        with pytest.raises(librdc.RdcError) as e:
+            librdc.rdc_create(4, 4, p, phi)
+        assert e.value.status == librdc.RDC_EINVAL
+
+
+def test_status_strings(librdc):
+    for code in range(8):
+        assert librdc.rdc_status_str(code).startswith("RDC_")

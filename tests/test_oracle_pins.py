@@ -55,3 +55,40 @@ def test_stability_reading_phi02(orc, om):
     assert 1e-9 < dev < 1e-2
     J54 = P.analytic_jacobian(orc.rest_state(0.054), orc.rest_state(0.054), 0.054)
     assert np.max(np.abs(1 + P.DT * np.linalg.eigvals(J54))) < 1.0
+
+
+# ---------------------------------------------------------------------------
+# the paper's qualitative circuits on the oracle (§4.1, §4.2)
+# ---------------------------------------------------------------------------
+
+def _arrival(orc, c, fire, probe, steps):
+    import os
+    u, v = orc.rest_field(c.phi)
+    for name in fire:
+        cx, cy, r = c.seeds[name]
+        orc.seed_disk(u, cx, cy, r, 0.8)
+    return orc.run(c.phi, u, v, steps, nthreads=min(8, os.cpu_count() or 1),
+                   probes=[c.probes[probe]])["t_arr"][0]
+
+
+def test_and_gate_truth_table_oracle(orc):
+    """§4.1: a single input does not reach the output (01 -> 0, 10 -> 0),
+    two colliding inputs do (11 -> 1); no input, no output."""
+    import rdc_inputs as ri
+    c = ri.and_gate(160, 128, arm=50, out_len=40)
+    steps = 9000
+    assert _arrival(orc, c, [], "out", steps) < 0
+    assert _arrival(orc, c, ["A"], "out", steps) < 0
+    assert _arrival(orc, c, ["B"], "out", steps) < 0
+    assert _arrival(orc, c, ["A", "B"], "out", steps) > 0
+
+
+@pytest.mark.parametrize("flip", [False, True])
+def test_diode_direction_oracle(orc, flip):
+    """§4.2: a wave passes from the anode (flat side) to the cathode (pointed
+    side) and not from the cathode to the anode."""
+    import rdc_inputs as ri
+    c = ri.diode(flip=flip)
+    steps = 12000
+    assert _arrival(orc, c, ["anode"], "cathode_end", steps) > 0
+    assert _arrival(orc, c, ["cathode"], "anode_end", steps) < 0
