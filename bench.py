@@ -133,9 +133,16 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(cells_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job GCUPS: every rank advanced its own copy of the workload, the
+    job took as long as the slowest rank."""
+    return world * cells_per_rank / t_max / 1e9
 
 
 # ---------------------------------------------------------------------------
@@ -207,6 +214,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the temporal-blocking / storage-mode / e2e lines")
+    ap.add_argument("--kblock", type=int, default=1,
+                    help="Euler steps per launch of the timed kernel (1 = single-step kernel)")
     ap.add_argument("--grid", type=int, default=None,
                     help="square grid size (default 8192); smaller sizes are for profiling")
     args = ap.parse_args()
@@ -227,7 +236,7 @@ def main():
     # a dedicated stream: the simulation and the CUDA events share it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    p = pkg.rdc_params_default(precision=pkg.RDC_F32, k_block=1)
+    p = pkg.rdc_params_default(precision=pkg.RDC_F32, k_block=args.kblock)
     h = pkg.rdc_create(W, H, p, None, stream.cuda_stream)
     disks = ri.random_disks(DISK_SEED, N_DISKS, W, H)
     nE = args.euler_steps
@@ -268,10 +277,11 @@ def main():
     t_max = max_over_ranks(elapsed, world)
 
     cells = W * H * nE * args.steps
-    value = world * cells / t_max / 1e9
+    value = weak_scaling_value(cells, world, t_max)
     ms_per_step = t_max / args.steps * 1e3
     peak, peak_kind = _peaks()
     per_launch_s = step_kernel_s / launches
+    # one launch moves the state once whatever k is (k Euler steps per launch)
     bytes_per_launch = BYTES_PER_CELL["f32"] * W * H
     achieved = bytes_per_launch / per_launch_s / 1e9
 
@@ -284,7 +294,8 @@ def main():
         modes = {m: _mode_gcups(pkg, stream, m, 1, 1000) for m in ("bf16", "f16")}
         modes["bf16_k4"] = _mode_gcups(pkg, stream, "bf16", 4, 1000)
         modes["f64"] = _mode_gcups(pkg, stream, "f64", 1, 100)
-        extras = {"temporal_blocking_gcups": tb, "storage_modes_gcups": modes}
+        extras = {"temporal_blocking_gcups": tb, "storage_modes_gcups": modes,
+                  "batch_sweep": _batch_sweep(pkg, stream), "serving": _serving(pkg)}
     e2e = None if args.no_extras else _e2e(pkg, stream, h, disks, nE, args)
 
     pkg.rdc_destroy(h)
@@ -302,12 +313,14 @@ def main():
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"oregonator_{W}x{H}_phi0.054_200disks",
                            "grid": [W, H], "euler_steps_per_bench_step": nE,
-                           "kernel": "single-step (k=1)", "precision": "f32",
+                           "kernel": ("single-step (k=1)" if args.kblock == 1 else
+                                      f"temporally blocked (k={args.kblock})"),
+                           "precision": "f32",
                            "l2": "inputs larger than L2 (1.34 GB state), no flush"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": peak_kind, "traffic": None,
-                             "kernel": "k_step1<float>",
+                             "kernel": "k_step1<float>" if args.kblock == 1 else "k_stepk_stream<float>",
                              "bytes_per_cell_update": BYTES_PER_CELL["f32"],
                              "launch_us": per_launch_s * 1e6},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -339,6 +352,65 @@ def _mode_gcups(pkg, stream, mode, k, n):
         return W * H * n / (a.elapsed_time(b) / 1e3) / 1e9
     finally:
         pkg.rdc_destroy(h)
+
+
+def _batch_sweep(pkg, stream, steps=5000):
+    """Parameter sweep: 512 grids of sizes U{128, 256, 512, 1024}^2, phi ~
+    U[0.05, 0.08], eps ~ U[0.02, 0.03], 1-8 disks each (PCG64 seed 4); the
+    autotuner picks the launch shape, then `steps` Euler steps run as one CUDA
+    graph of persistent launches over all grids."""
+    import torch
+    spec = ri.sweep_batch(seed=4, n_grids=512)
+    grids = [(n, n) for n in spec.sizes]
+    params = [pkg.rdc_params_default(precision=0, eps=e) for e in spec.eps]
+    phis = [np.full((n, n), ph, dtype=np.float32) for n, ph in zip(spec.sizes, spec.phi)]
+    b = pkg.rdc_batch_create(grids, params, phis, stream=stream.cuda_stream)
+    try:
+        for i, disks in enumerate(spec.disks):
+            for (cx, cy, r) in disks:
+                pkg.rdc_batch_seed(b, i, cx, cy, r, ri.SEED_VALUE)
+        t0 = time.perf_counter()
+        info = pkg.rdc_batch_tune(b, 3)
+        tune_s = time.perf_counter() - t0
+        pkg.rdc_batch_step(b, None, steps)          # captures the graph (and warms up)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pkg.rdc_batch_step(b, None, steps)          # graph replay
+        z.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(z) / 1e3
+        bad = sum(pkg.rdc_batch_check(b, i)[0] != 0 for i in range(len(grids)))
+        cells = float(sum(n * n for n in spec.sizes))
+        return {"gcups": cells * steps / sec / 1e9, "seconds": sec, "grids": len(grids),
+                "cells": cells, "steps": steps, "k": info.k, "rows": info.rows,
+                "krows": info.krows, "tuned_gcups": info.tuned_gcups,
+                "tune_seconds": tune_s, "unhealthy_grids": int(bad)}
+    finally:
+        pkg.rdc_batch_destroy(b)
+
+
+def _serving(pkg, frames=20, steps_per_frame=50):
+    """Interactive serving: 64 sessions arriving Poisson at 20/s (seed 5),
+    grids U{512, 1024, 2048}^2 with diode maps at random positions and
+    orientations, each requesting `frames` frames of `steps_per_frame` steps
+    with a u = 0.8 touch before each; continuous batching on one stream."""
+    from paper_1901_06535_gb300 import serve
+    specs = ri.diode_sessions(seed=5, n=64, frames=frames)
+    sessions = [serve.Session(s.sid, s.size, s.size, phi=s.phi, frames=frames,
+                              touches=s.touches) for s in specs]
+    srv = serve.Server(precision=0, k_block=2, steps_per_frame=steps_per_frame)
+    try:
+        wall, st = serve.run_workload(sessions, [s.arrival for s in specs], srv)
+    finally:
+        srv.close()
+    st["wall_seconds"] = wall
+    st["gcups"] = st["cells_stepped"] / wall / 1e9
+    st["sessions"] = len(sessions)
+    st["frames_per_session"] = frames
+    st["steps_per_frame"] = steps_per_frame
+    return st
 
 
 def _e2e(pkg, stream, h, disks, nE, args):

@@ -187,10 +187,11 @@ int rdc_set_state(rdc_sim* sim, const void* u_host, const void* v_host,
  *     u'  = c + dt * (R/eps + Du*lap)     (flags drop one of the two terms)
  *     v'  = v + dt * (c - v)
  * RDC_F64 evaluates exactly this sequence in FP64 with IEEE division and no
- * fused multiply-add.  The FP32 modes evaluate it in FP32 with IEEE
- * division and a fixed set of fused multiply-adds, and round u', v' to the
- * storage type after every step.  Every k_block and launch shape gives the
- * same bits.
+ * fused multiply-add.  The FP32 modes evaluate it in FP32: rat with IEEE
+ * division, R/eps as R times 1/eps (rounded once to FP32, as Eq. 1 writes the
+ * bracket scaled by 1/eps) fused with Du*lap, a fixed set of fused
+ * multiply-adds elsewhere; u', v' are rounded to the storage type after every
+ * step.  Every k_block and launch shape gives the same bits.
  */
 int rdc_step(rdc_sim* sim, int64_t n);
 
@@ -274,6 +275,10 @@ typedef struct {
     int32_t k;         /* Euler steps per launch, 1..8 (1 = single-step
                           kernel only); the tile's shared memory,
                           4 (tx + 2k)(ty + 2k) values, must fit in 227 KB */
+    int32_t variant;   /* kernel for k > 1: 0 = register-streamed (every
+                          intermediate level in registers; full model only,
+                          test modes fall back to 1), 1 = shared-memory tile */
+    int32_t krows;     /* register-streamed kernel: rows marched per CTA, >= 1 */
 } rdc_launch_shape;
 
 /* Current launch shapes (set at create from the grid size and k_block). */
@@ -281,6 +286,99 @@ int rdc_get_shape(rdc_sim* sim, rdc_launch_shape* out);
 
 /* Replaces the launch shapes; RDC_EINVAL (and no change) if out of range. */
 int rdc_set_shape(rdc_sim* sim, const rdc_launch_shape* in);
+
+/* ---- batches of independent grids ---------------------------------------- */
+/*
+ * A batch holds many independent simulations (parameter sweeps, interactive
+ * sessions) and advances any subset of them with persistent launches over
+ * all their cells at once.  Each grid has its own size, phi map and model
+ * parameters (eps, f, q, Du, dt, dx); all grids of a batch share the
+ * precision, the full model (flags 0) and k_block.  A grid's result is
+ * bit-identical to an rdc_sim with the same parameters and inputs, whatever
+ * else runs in the batch and whatever the launch configuration.
+ */
+typedef struct rdc_batch rdc_batch;
+
+typedef struct {
+    int32_t ngrids;        /* live grids */
+    int32_t slots;         /* live + free slots; grid indices are < slots */
+    int32_t precision;
+    int32_t k;             /* Euler steps per launch (1 = single-step kernel) */
+    int32_t rows;          /* rows per work item, single-step kernel */
+    int32_t krows;         /* rows per work item, k-step kernel */
+    int32_t graphs;        /* 1 = step sequences run as cached CUDA graphs */
+    int32_t reserved;
+    double total_cells;    /* cells over live grids */
+    int64_t launches;      /* step-kernel launches enqueued so far */
+    int64_t graph_launches;
+    double cells_stepped;  /* cell-updates enqueued so far */
+    double tuned_gcups;    /* set by rdc_batch_tune: best rate measured */
+    void* stream;          /* the batch's cudaStream_t */
+} rdc_batch_info;
+
+/*
+ * Creates a batch of n >= 0 grids.  grids[i], params[i] describe grid i
+ * (validated as in rdc_create; params[i].precision and k_block must equal
+ * params[0]'s and flags must be 0); phi_host is NULL (every map uniform
+ * phi_active) or n pointers, each NULL or an H*W float map (copied).  With
+ * n = 0, params must still point at one rdc_params giving the precision and
+ * k_block of the grids to come.  Every grid starts at its rest state.
+ * stream as for rdc_create.  Grid indices are 0..n-1.
+ */
+int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
+                     const float* const* phi_host, void* stream, rdc_batch** out);
+
+/* Adds one grid (allocates its planes; rest state) and returns its index in
+ * *idx (a freed slot is reused).  RDC_ENOMEM if the device memory is short. */
+int rdc_batch_add(rdc_batch* b, rdc_grid g, const rdc_params* p, const float* phi_host,
+                  int32_t* idx);
+
+/* Removes grid idx and frees its memory (waits for the batch's stream). */
+int rdc_batch_remove(rdc_batch* b, int32_t idx);
+
+/* Waits for the batch's stream, frees everything.  NULL is a no-op. */
+void rdc_batch_destroy(rdc_batch* b);
+
+/* Async.  Stimulation of grid idx, as rdc_seed. */
+int rdc_batch_seed(rdc_batch* b, int32_t idx, double cx, double cy, double r, double value);
+
+/* Sets grid idx's current state from packed host arrays, as rdc_set_state. */
+int rdc_batch_set_state(rdc_batch* b, int32_t idx, const void* u_host, const void* v_host,
+                        int32_t dtype);
+
+/*
+ * Async.  Advances the m grids idx[0..m-1] (distinct, live; idx = NULL: every
+ * live grid) by n >= 0 Euler steps: n / k launches of the k-step kernel and
+ * n % k single-step launches, each a persistent launch over warp-sized work
+ * items of all those grids.  With graphs on (the default) the launch sequence
+ * for a given (subset, n, shape) is captured once into a CUDA graph and
+ * replayed afterwards.
+ */
+int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n);
+
+/* Synchronous.  Health check of grid idx, as rdc_check. */
+int rdc_batch_check(rdc_batch* b, int32_t idx, int64_t* first_bad);
+
+/* Synchronous.  Grid idx's state into host arrays, as rdc_read. */
+int rdc_batch_read(rdc_batch* b, int32_t idx, void* u_out, void* v_out, int32_t dtype);
+
+/* Waits for the batch's stream. */
+int rdc_batch_sync(rdc_batch* b);
+
+/* Launch configuration: k (1..8), rows and krows (>= 1), graphs (0/1).  Any
+ * valid configuration gives the same bits. */
+int rdc_batch_set_config(rdc_batch* b, int32_t k, int32_t rows, int32_t krows, int32_t graphs);
+
+int rdc_batch_get_info(rdc_batch* b, rdc_batch_info* out);
+
+/*
+ * Autotuner: times reps launches of each candidate (single step with 8, 16 or
+ * 32 rows per item; k in {2, 3, 4, 6, 8} with 32..256 rows per item) over all
+ * live grids, keeps the fastest in cell-updates per second, and reports it in
+ * *out (optional).  Every timed launch reads the current buffers and writes
+ * the spare ones, so tuning does not advance or change any grid's state.
+ */
+int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out);
 
 /* Human-readable name of a status code (static storage). */
 const char* rdc_status_str(int status);

@@ -12,12 +12,16 @@ import numpy as np
 
 from ._capi import (  # noqa: F401  (re-exported C-ABI names)
     RDC_DIFFUSION_ONLY, RDC_DTYPE_BF16, RDC_DTYPE_F16, RDC_DTYPE_F32, RDC_DTYPE_F64,
-    RDC_EINVAL, RDC_ENONFINITE, RDC_EUNSTABLE_WARN, RDC_F32, RDC_F32_BF16STORE,
+    RDC_ECUDA, RDC_EINVAL, RDC_ENOMEM, RDC_ENONFINITE, RDC_ETIMEOUT, RDC_EUNSTABLE_WARN,
+    RDC_EUNSUPPORTED, RDC_F32, RDC_F32_BF16STORE,
     RDC_F32_F16STORE, RDC_F64, RDC_OK, RDC_REACTION_ONLY, PRECISION_NAMES, RdcError,
     lib, rdc_check, rdc_create, rdc_create_ext, rdc_create_f64phi, rdc_destroy,
     rdc_get_shape, rdc_get_view, rdc_last_error, rdc_params, rdc_params_default,
     rdc_probe, rdc_read, rdc_reset_rest, rdc_rest_state, rdc_seed, rdc_set_phi,
-    rdc_set_shape, rdc_set_state, rdc_stability, rdc_status_str, rdc_step, rdc_sync)
+    rdc_set_shape, rdc_set_state, rdc_stability, rdc_status_str, rdc_step,
+    rdc_sync, rdc_batch_add, rdc_batch_check, rdc_batch_create, rdc_batch_destroy,
+    rdc_batch_get_info, rdc_batch_read, rdc_batch_remove, rdc_batch_seed, rdc_batch_set_config,
+    rdc_batch_set_state, rdc_batch_step, rdc_batch_sync, rdc_batch_tune)
 
 
 class Sim:
@@ -88,7 +92,7 @@ class Sim:
         cur = self.shape()
         cur.update(kw)
         rdc_set_shape(self.handle, cur["bx"], cur["rows"], cur["tx"], cur["ty"],
-                      cur["nthreads"], cur["k"])
+                      cur["nthreads"], cur["k"], cur["variant"], cur["krows"])
 
     def view(self):
         return rdc_get_view(self.handle)

@@ -71,7 +71,21 @@ class rdc_view(ctypes.Structure):
 class rdc_launch_shape(ctypes.Structure):
     _fields_ = [("bx", ctypes.c_int32), ("rows", ctypes.c_int32),
                 ("tx", ctypes.c_int32), ("ty", ctypes.c_int32),
-                ("nthreads", ctypes.c_int32), ("k", ctypes.c_int32)]
+                ("nthreads", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("krows", ctypes.c_int32)]
+
+
+class rdc_batch_info(ctypes.Structure):
+    _fields_ = [("ngrids", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("rows", ctypes.c_int32), ("krows", ctypes.c_int32),
+                ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("total_cells", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("cells_stepped", ctypes.c_double),
+                ("tuned_gcups", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class RdcError(RuntimeError):
@@ -111,6 +125,23 @@ _SIGS = {
     "rdc_get_view": (ctypes.c_int, [_P, ctypes.POINTER(rdc_view)]),
     "rdc_get_shape": (ctypes.c_int, [_P, ctypes.POINTER(rdc_launch_shape)]),
     "rdc_set_shape": (ctypes.c_int, [_P, ctypes.POINTER(rdc_launch_shape)]),
+    "rdc_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(rdc_params), _P, _P,
+                                        ctypes.POINTER(_P)]),
+    "rdc_batch_add": (ctypes.c_int, [_P, rdc_grid, ctypes.POINTER(rdc_params), _P,
+                                     ctypes.POINTER(ctypes.c_int32)]),
+    "rdc_batch_remove": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "rdc_batch_destroy": (None, [_P]),
+    "rdc_batch_seed": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double]),
+    "rdc_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
+    "rdc_batch_step": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64]),
+    "rdc_batch_check": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
+    "rdc_batch_read": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
+    "rdc_batch_sync": (ctypes.c_int, [_P]),
+    "rdc_batch_set_config": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32]),
+    "rdc_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(rdc_batch_info)]),
+    "rdc_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_batch_info)]),
     "rdc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "rdc_last_error": (ctypes.c_char_p, []),
 }
@@ -340,6 +371,118 @@ def rdc_get_shape(h) -> rdc_launch_shape:
     return s
 
 
-def rdc_set_shape(h, bx: int, rows: int, tx: int, ty: int, nthreads: int, k: int) -> int:
-    s = rdc_launch_shape(bx, rows, tx, ty, nthreads, k)
+def rdc_set_shape(h, bx: int, rows: int, tx: int, ty: int, nthreads: int, k: int,
+                  variant: int = 0, krows: int = 256) -> int:
+    s = rdc_launch_shape(bx, rows, tx, ty, nthreads, k, variant, krows)
     return _chk(lib().rdc_set_shape(h, ctypes.byref(s)), "rdc_set_shape")
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+
+def rdc_batch_create(grids, params, phis=None, stream=None):
+    """grids: list of (width, height); params: list of rdc_params (one per
+    grid; for an empty batch a single rdc_params); phis: None or a list of
+    host float32 maps / None.  Returns a handle."""
+    n = len(grids)
+    G = (rdc_grid * max(n, 1))(*[rdc_grid(int(w), int(h)) for w, h in grids])
+    plist = list(params) if n > 0 else [params[0] if isinstance(params, (list, tuple)) else params]
+    P = (rdc_params * len(plist))(*plist)
+    keep = []
+    if phis is None:
+        phi_arr = None
+    else:
+        arr = (_P * n)()
+        for i, ph in enumerate(phis):
+            if ph is None:
+                arr[i] = None
+            else:
+                a = np.ascontiguousarray(ph, dtype=np.float32)
+                keep.append(a)
+                arr[i] = a.ctypes.data
+        phi_arr = arr
+    h = _P()
+    rc = lib().rdc_batch_create(n, G, P, phi_arr, _stream(stream), ctypes.byref(h))
+    _chk(rc, "rdc_batch_create")
+    return h.value
+
+
+def rdc_batch_add(b, width: int, height: int, params: rdc_params, phi=None) -> int:
+    idx = ctypes.c_int32(-1)
+    ptr = None
+    if phi is not None:
+        a = np.ascontiguousarray(phi, dtype=np.float32)
+        if a.shape != (height, width):
+            raise ValueError("phi shape mismatch")
+        ptr = a.ctypes.data
+    rc = lib().rdc_batch_add(b, rdc_grid(int(width), int(height)), ctypes.byref(params), ptr,
+                             ctypes.byref(idx))
+    _chk(rc, "rdc_batch_add")
+    return idx.value
+
+
+def rdc_batch_remove(b, idx: int) -> int:
+    return _chk(lib().rdc_batch_remove(b, int(idx)), "rdc_batch_remove")
+
+
+def rdc_batch_destroy(b) -> None:
+    if b:
+        lib().rdc_batch_destroy(b)
+
+
+def rdc_batch_seed(b, idx: int, cx: float, cy: float, r: float, value: float) -> int:
+    return _chk(lib().rdc_batch_seed(b, int(idx), float(cx), float(cy), float(r), float(value)),
+                "rdc_batch_seed")
+
+
+def rdc_batch_set_state(b, idx: int, u=None, v=None) -> int:
+    pu, cu, _ = _host_ptr(u, "u")
+    pv, cv, _ = _host_ptr(v, "v")
+    code = cu if cu is not None else cv
+    if code is None:
+        return RDC_OK
+    return _chk(lib().rdc_batch_set_state(b, int(idx), pu, pv, code), "rdc_batch_set_state")
+
+
+def rdc_batch_step(b, idx=None, n: int = 1) -> int:
+    if idx is None:
+        return _chk(lib().rdc_batch_step(b, None, 0, int(n)), "rdc_batch_step")
+    a = np.ascontiguousarray(idx, dtype=np.int32)
+    return _chk(lib().rdc_batch_step(b, a.ctypes.data, len(a), int(n)), "rdc_batch_step")
+
+
+def rdc_batch_check(b, idx: int):
+    fb = ctypes.c_int64(-1)
+    rc = _chk(lib().rdc_batch_check(b, int(idx), ctypes.byref(fb)), "rdc_batch_check",
+              allow=(RDC_ENONFINITE,))
+    return rc, fb.value
+
+
+def rdc_batch_read(b, idx: int, u_out=None, v_out=None) -> int:
+    pu, cu, _ = _host_ptr(u_out, "u_out")
+    pv, cv, _ = _host_ptr(v_out, "v_out")
+    code = cu if cu is not None else (cv if cv is not None else RDC_DTYPE_F64)
+    return _chk(lib().rdc_batch_read(b, int(idx), pu, pv, code), "rdc_batch_read",
+                allow=(RDC_ENONFINITE,))
+
+
+def rdc_batch_sync(b) -> int:
+    return _chk(lib().rdc_batch_sync(b), "rdc_batch_sync")
+
+
+def rdc_batch_set_config(b, k: int, rows: int, krows: int, graphs: bool = True) -> int:
+    return _chk(lib().rdc_batch_set_config(b, int(k), int(rows), int(krows), int(bool(graphs))),
+                "rdc_batch_set_config")
+
+
+def rdc_batch_get_info(b) -> rdc_batch_info:
+    info = rdc_batch_info()
+    _chk(lib().rdc_batch_get_info(b, ctypes.byref(info)), "rdc_batch_get_info")
+    return info
+
+
+def rdc_batch_tune(b, reps: int = 3) -> rdc_batch_info:
+    info = rdc_batch_info()
+    _chk(lib().rdc_batch_tune(b, int(reps), ctypes.byref(info)), "rdc_batch_tune")
+    return info

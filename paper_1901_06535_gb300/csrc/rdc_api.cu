@@ -16,6 +16,7 @@
 #include <new>
 
 #include "rdc.h"
+#include "rdc_host.h"
 #include "rdc_internal.h"
 
 namespace rdc {
@@ -31,8 +32,58 @@ size_t stepk_smem_f32(ShapeK);
 size_t stepk_smem_f64(ShapeK);
 size_t stepk_smem_bf16(ShapeK);
 size_t stepk_smem_f16(ShapeK);
-cudaError_t launch_fill_phi(int prec, void* dst, int W, int H, int64_t pitch,
-                            double value, cudaStream_t st);
+cudaError_t launch_stream_f32(const Planes&, const ModelD&, int, int, cudaStream_t);
+cudaError_t launch_stream_f64(const Planes&, const ModelD&, int, int, cudaStream_t);
+cudaError_t launch_stream_bf16(const Planes&, const ModelD&, int, int, cudaStream_t);
+cudaError_t launch_stream_f16(const Planes&, const ModelD&, int, int, cudaStream_t);
+#define RDC_DECL_BATCH(n)                                                                   \
+    cudaError_t launch_batch_step1_##n(const GridDesc*, const Item*, int, int, int,         \
+                                       cudaStream_t);                                       \
+    cudaError_t launch_batch_stream_##n(const GridDesc*, const Item*, int, int, int, int,   \
+                                        cudaStream_t);                                      \
+    int batch_stream_outc_##n(int);
+RDC_DECL_BATCH(f32)
+RDC_DECL_BATCH(f64)
+RDC_DECL_BATCH(bf16)
+RDC_DECL_BATCH(f16)
+#undef RDC_DECL_BATCH
+
+cudaError_t launch_batch_step1(int prec, const GridDesc* d, const Item* items, int nitems,
+                               int j, int ctas, cudaStream_t st)
+{
+    switch (prec) {
+        case P_F32: return launch_batch_step1_f32(d, items, nitems, j, ctas, st);
+        case P_F64: return launch_batch_step1_f64(d, items, nitems, j, ctas, st);
+        case P_BF16: return launch_batch_step1_bf16(d, items, nitems, j, ctas, st);
+        case P_F16: return launch_batch_step1_f16(d, items, nitems, j, ctas, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_stream(int prec, const GridDesc* d, const Item* items, int nitems,
+                                int k, int j, int ctas, cudaStream_t st)
+{
+    switch (prec) {
+        case P_F32: return launch_batch_stream_f32(d, items, nitems, k, j, ctas, st);
+        case P_F64: return launch_batch_stream_f64(d, items, nitems, k, j, ctas, st);
+        case P_BF16: return launch_batch_stream_bf16(d, items, nitems, k, j, ctas, st);
+        case P_F16: return launch_batch_stream_f16(d, items, nitems, k, j, ctas, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int batch_step1_cols(int prec) { return 32 * vec_cells(prec); }
+
+int batch_stream_outc(int prec, int k)
+{
+    switch (prec) {
+        case P_F32: return batch_stream_outc_f32(k);
+        case P_F64: return batch_stream_outc_f64(k);
+        case P_BF16: return batch_stream_outc_bf16(k);
+        case P_F16: return batch_stream_outc_f16(k);
+    }
+    return 0;
+}
 
 cudaError_t launch_step1(int prec, int mode, const Planes& g, const ModelD& m,
                          Shape1 s, cudaStream_t st)
@@ -56,6 +107,25 @@ cudaError_t launch_stepk(int prec, int mode, const Planes& g, const ModelD& m,
         case P_F16: return launch_stepk_f16(mode, g, m, s, st);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_stream(int prec, const Planes& g, const ModelD& m, int k, int rows,
+                          cudaStream_t st)
+{
+    switch (prec) {
+        case P_F32: return launch_stream_f32(g, m, k, rows, st);
+        case P_F64: return launch_stream_f64(g, m, k, rows, st);
+        case P_BF16: return launch_stream_bf16(g, m, k, rows, st);
+        case P_F16: return launch_stream_f16(g, m, k, rows, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_kblock(int prec, int mode, const Planes& g, const ModelD& m, ShapeK s,
+                          cudaStream_t st)
+{
+    if (s.variant == 0 && mode == MODE_FULL) return launch_stream(prec, g, m, s.k, s.krows, st);
+    return launch_stepk(prec, mode, g, m, s, st);
 }
 
 size_t stepk_smem_bytes(int prec, ShapeK s)
@@ -104,7 +174,7 @@ struct rdc_sim {
 
 static thread_local char g_err[512] = "";
 
-static int cuda_fail(cudaError_t e, const char* what)
+int host_cuda_fail(cudaError_t e, const char* what)
 {
     std::snprintf(g_err, sizeof g_err, "%s: %s (%s)", what, cudaGetErrorName(e),
                   cudaGetErrorString(e));
@@ -114,7 +184,7 @@ static int cuda_fail(cudaError_t e, const char* what)
 #define CK(call, what)                               \
     do {                                             \
         cudaError_t e_ = (call);                     \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+        if (e_ != cudaSuccess) return host_cuda_fail(e_, what); \
     } while (0)
 
 static ModelD model_of(const rdc_params& p)
@@ -129,7 +199,7 @@ static ModelD model_of(const rdc_params& p)
     return m;
 }
 
-static bool params_valid(const rdc_params* p)
+bool host_params_valid(const rdc_params* p)
 {
     if (!p) return false;
     const double vals[6] = {p->eps, p->f, p->q, p->Du, p->dt, p->dx};
@@ -147,14 +217,14 @@ static bool params_valid(const rdc_params* p)
     return true;
 }
 
-static bool phi_ok(double phi, const rdc_params* p)
+bool host_phi_ok(double phi, const rdc_params* p)
 {
     return std::isfinite(phi) && phi > p->q * (1.0 + p->f);
 }
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-static int check_device()
+int host_check_device()
 {
     int dev = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
@@ -177,14 +247,22 @@ static void default_shapes(rdc_sim* s)
     int bx = 128;
     if (vecs < bx) bx = (int)std::max<int64_t>(32, round_up(vecs, 32));
     const int64_t ncb = (vecs + bx - 1) / bx;
-    int rows = 32;
-    while (rows > 4 && ncb * ((s->H + rows - 1) / rows) < 152 * 8) rows /= 2;
+    int rows = 8;
+    while (rows > 1 && ncb * ((s->H + rows - 1) / rows) < 152 * 8) rows /= 2;
     s->shape1 = Shape1{bx, rows};
     if (s->prec == P_F64)
         s->shapek = ShapeK{32, 32, 1, 256};
     else
         s->shapek = ShapeK{64, 32, 1, 256};
     s->shapek.k = s->p.k_block == 0 ? 1 : s->p.k_block;
+    s->shapek.variant = 0;
+    // rows per CTA of the streamed kernel: long enough that the 2k rows of
+    // overlap cost little, short enough for ~2.5 waves of warps (~24
+    // resident per SM)
+    int krows = 256;
+    while (krows > 32 && (int64_t)((s->W + 111) / 112) * ((s->H + krows - 1) / krows) < 152 * 48)
+        krows /= 2;
+    s->shapek.krows = krows;
 }
 
 static void destroy_impl(rdc_sim* s)
@@ -234,14 +312,14 @@ static int upload_phi(rdc_sim* s, const void* phi_host, int dtype)
 }
 
 // Validates a host phi map and returns its maximum.
-static bool scan_phi(const void* phi_host, int dtype, int64_t n, const rdc_params* p,
-                     double* mx)
+bool host_scan_phi(const void* phi_host, int dtype, int64_t n, const rdc_params* p,
+                  double* mx)
 {
     double m = -INFINITY;
     for (int64_t k = 0; k < n; ++k) {
         const double x = dtype == 0 ? (double)((const float*)phi_host)[k]
                                     : ((const double*)phi_host)[k];
-        if (!phi_ok(x, p)) return false;
+        if (!host_phi_ok(x, p)) return false;
         if (x > m) m = x;
     }
     *mx = m;
@@ -255,12 +333,12 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
 {
     if (!out) return RDC_EINVAL;
     *out = nullptr;
-    if (g.width < 1 || g.height < 1 || !params_valid(p)) return RDC_EINVAL;
+    if (g.width < 1 || g.height < 1 || !host_params_valid(p)) return RDC_EINVAL;
     const int64_t n = (int64_t)g.width * g.height;
     double phi_max = kPhiActive;
     if (phi_host) {
-        if (!scan_phi(phi_host, phi_dtype, n, p, &phi_max)) return RDC_EINVAL;
-    } else if (!ext_u && !phi_ok(kPhiActive, p)) {
+        if (!host_scan_phi(phi_host, phi_dtype, n, p, &phi_max)) return RDC_EINVAL;
+    } else if (!ext_u && !host_phi_ok(kPhiActive, p)) {
         return RDC_EINVAL;
     }
     const int prec = p->precision;
@@ -274,7 +352,7 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
             ext_pitch_bytes % esz)
             return RDC_EINVAL;
     }
-    int rc = check_device();
+    int rc = host_check_device();
     if (rc) return rc;
 
     rdc_sim* s = new (std::nothrow) rdc_sim();
@@ -291,7 +369,7 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
         cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             delete s;
-            return cuda_fail(e, "cudaStreamCreateWithFlags");
+            return host_cuda_fail(e, "cudaStreamCreateWithFlags");
         }
         s->owns_stream = true;
     }
@@ -306,7 +384,7 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
         cudaError_t e = cudaMalloc((void**)&s->misc, kMiscBytes);
         if (e != cudaSuccess) {
             destroy_impl(s);
-            return cuda_fail(e, "cudaMalloc(scratch)");
+            return host_cuda_fail(e, "cudaMalloc(scratch)");
         }
         s->owns_misc = true;
     } else {
@@ -317,7 +395,7 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
         cudaError_t e = cudaMalloc(&s->base, total);
         if (e != cudaSuccess) {
             destroy_impl(s);
-            return cuda_fail(e, "cudaMalloc(planes)");
+            return host_cuda_fail(e, "cudaMalloc(planes)");
         }
         s->owns = true;
         unsigned char* b = (unsigned char*)s->base;
@@ -330,22 +408,22 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
         e = cudaMemsetAsync(s->base, 0, total, s->stream);
         if (e != cudaSuccess) {
             destroy_impl(s);
-            return cuda_fail(e, "cudaMemsetAsync");
+            return host_cuda_fail(e, "cudaMemsetAsync");
         }
         if (phi_host) {
             rc = upload_phi(s, phi_host, phi_dtype);
         } else {
             e = launch_fill_phi(prec, s->phi, s->W, s->H, s->pitch, kPhiActive, s->stream);
-            rc = e == cudaSuccess ? RDC_OK : cuda_fail(e, "phi fill kernel");
+            rc = e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "phi fill kernel");
         }
         if (rc == RDC_OK) {
             e = launch_rest(prec, s->u[0], s->v[0], s->phi, s->W, s->H, s->pitch, p->f,
                             p->q, s->stream);
-            rc = e == cudaSuccess ? RDC_OK : cuda_fail(e, "rest-state kernel");
+            rc = e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "rest-state kernel");
         }
         if (rc == RDC_OK) {
             e = cudaStreamSynchronize(s->stream);
-            rc = e == cudaSuccess ? RDC_OK : cuda_fail(e, "cudaStreamSynchronize");
+            rc = e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "cudaStreamSynchronize");
         }
         if (rc != RDC_OK) {
             destroy_impl(s);
@@ -413,7 +491,7 @@ int rdc_set_phi(rdc_sim* s, const void* phi_host, int32_t dtype)
 {
     if (!s || !phi_host || (dtype != 0 && dtype != 1)) return RDC_EINVAL;
     double mx = 0.0;
-    if (!scan_phi(phi_host, dtype, (int64_t)s->W * s->H, &s->p, &mx)) return RDC_EINVAL;
+    if (!host_scan_phi(phi_host, dtype, (int64_t)s->W * s->H, &s->p, &mx)) return RDC_EINVAL;
     int rc = upload_phi(s, phi_host, dtype);
     if (rc) return rc;
     s->phi_max = mx;
@@ -467,13 +545,13 @@ int rdc_step(rdc_sim* s, int64_t n)
         cudaError_t e;
         int done;
         if (k > 1 && left >= k) {
-            e = launch_stepk(s->prec, s->mode, g, m, s->shapek, s->stream);
+            e = launch_kblock(s->prec, s->mode, g, m, s->shapek, s->stream);
             done = k;
         } else {
             e = launch_step1(s->prec, s->mode, g, m, s->shape1, s->stream);
             done = 1;
         }
-        if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+        if (e != cudaSuccess) return host_cuda_fail(e, "step kernel");
         s->cur = 1 - s->cur;
         s->steps_done += done;
         s->launches += 1;
@@ -626,6 +704,8 @@ int rdc_get_shape(rdc_sim* s, rdc_launch_shape* out)
     out->ty = s->shapek.ty;
     out->nthreads = s->shapek.nthreads;
     out->k = s->shapek.k;
+    out->variant = s->shapek.variant;
+    out->krows = s->shapek.krows;
     return RDC_OK;
 }
 
@@ -636,8 +716,10 @@ int rdc_set_shape(rdc_sim* s, const rdc_launch_shape* in)
     if (in->k < 1 || in->k > 8 || in->tx < 1 || in->ty < 1 || in->nthreads < 32 ||
         in->nthreads > 512 || in->nthreads % 32)
         return RDC_EINVAL;
-    ShapeK sk{in->tx, in->ty, in->k, in->nthreads};
+    if (in->variant < 0 || in->variant > 1 || in->krows < 1) return RDC_EINVAL;
+    ShapeK sk{in->tx, in->ty, in->k, in->nthreads, in->variant, in->krows};
     if (in->k > 1 && stepk_smem_bytes(s->prec, sk) > 227 * 1024) return RDC_EINVAL;
+    if (in->k > 1 && (s->H + in->krows - 1) / in->krows > 65535) return RDC_EINVAL;
     if (in->k > 1 && (s->H + in->ty - 1) / in->ty > 65535) return RDC_EINVAL;
     s->shape1 = Shape1{in->bx, in->rows};
     s->shapek = sk;

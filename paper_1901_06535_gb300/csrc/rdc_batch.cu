@@ -1,0 +1,651 @@
+// Batches of independent grids (parameter sweeps, many sessions): one device
+// allocation per grid (grids can join and leave), a device table of grid
+// descriptors, persistent launches over warp-sized work items of all grids
+// at once, CUDA graphs of whole step sequences, and an autotuner for the
+// launch shape.
+//
+// Each grid in a batch runs the same cell_update as a single simulation with
+// the same parameters, so a grid's result is bit-identical whether it is
+// stepped alone, in a batch, or in any subset of one.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "rdc.h"
+#include "rdc_host.h"
+#include "rdc_internal.h"
+
+using namespace rdc;
+
+namespace {
+
+const double kPhiActive = 0.054;  // Table 1
+
+struct Config {
+    int k = 1;       // Euler steps per launch
+    int rows = 16;   // rows per item, single-step kernel
+    int krows = 64;  // rows per item, streamed k-step kernel
+};
+
+struct ItemList {
+    Item* dev = nullptr;
+    int n = 0;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+};
+
+}  // namespace
+
+struct rdc_batch {
+    int n = 0;                       // slots (live or free)
+    int prec = 0;
+    int k_block = 0;
+    std::vector<rdc_grid> grids;
+    std::vector<rdc_params> params;
+    std::vector<GridDesc> desc;      // host copy; par kept current
+    std::vector<void*> mem;          // per-slot allocation (nullptr = free slot)
+    GridDesc* d_desc = nullptr;
+    int d_desc_cap = 0;
+    unsigned long long* d_flag = nullptr;
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    Config cfg;
+    bool use_graphs = true;
+    // work lists over every live grid (rebuilt when grids join or leave or
+    // the shape changes) and graphs of launch sequences, keyed by
+    // (n, k, rows, krows); the subset of a call is in the descriptors
+    ItemList step1_items, stream_items;
+    std::map<std::vector<int64_t>, GraphEntry> graphs;
+    int64_t launches = 0;
+    int64_t graph_launches = 0;
+    double cells_stepped = 0.0;
+};
+
+namespace {
+
+void free_items(ItemList& L)
+{
+    if (L.dev) cudaFree(L.dev);
+    L.dev = nullptr;
+    L.n = 0;
+}
+
+void free_graphs(rdc_batch* b)
+{
+    for (auto& kv : b->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    b->graphs.clear();
+}
+
+int persistent_ctas(int nitems)
+{
+    // 128-thread CTAs, 4 warps each; enough CTAs to fill every SM several
+    // times over, never more than the items need
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int want = sms * 8;
+    const int need = (nitems + 3) / 4;
+    return std::max(1, std::min(want, need));
+}
+
+int build_items(rdc_batch* b, bool stream, ItemList* out)
+{
+    std::vector<Item> items;
+    const int cols = stream ? batch_stream_outc(b->prec, b->cfg.k) : batch_step1_cols(b->prec);
+    const int rows = stream ? b->cfg.krows : b->cfg.rows;
+    if (cols <= 0 || rows <= 0) return RDC_EINVAL;
+    for (int g = 0; g < b->n; ++g) {
+        if (!b->mem[g]) continue;
+        const int W = b->grids[g].width, H = b->grids[g].height;
+        for (int y0 = 0; y0 < H; y0 += rows)
+            for (int x0 = 0; x0 < W; x0 += cols)
+                items.push_back(Item{g, x0, y0, std::min(y0 + rows, H)});
+    }
+    out->n = (int)items.size();
+    if (items.empty()) return RDC_OK;
+    cudaError_t e = cudaMalloc(&out->dev, items.size() * sizeof(Item));
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(items)");
+    e = cudaMemcpyAsync(out->dev, items.data(), items.size() * sizeof(Item),
+                        cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMemcpyAsync(items)");
+    return RDC_OK;
+}
+
+int get_items(rdc_batch* b, bool stream, ItemList** out)
+{
+    ItemList& L = stream ? b->stream_items : b->step1_items;
+    if (!L.dev) {
+        int rc = build_items(b, stream, &L);
+        if (rc) return rc;
+    }
+    *out = &L;
+    return RDC_OK;
+}
+
+// Enqueues the launch sequence of n steps for the subset: n / k streamed
+// k-step launches, then n % k single steps; launch j reads buffer
+// (par + j) & 1 of each grid.
+int enqueue_sequence(rdc_batch* b, int64_t n, int64_t* launches)
+{
+    const int k = b->cfg.k;
+    ItemList* s1 = nullptr;
+    ItemList* sk = nullptr;
+    int rc = get_items(b, false, &s1);
+    if (rc) return rc;
+    if (k > 1) {
+        rc = get_items(b, true, &sk);
+        if (rc) return rc;
+    }
+    int64_t j = 0, left = n;
+    while (left > 0) {
+        cudaError_t e;
+        if (k > 1 && left >= k) {
+            e = launch_batch_stream(b->prec, b->d_desc, sk->dev, sk->n, k, (int)(j & 1),
+                                    persistent_ctas(sk->n), b->stream);
+            left -= k;
+        } else {
+            e = launch_batch_step1(b->prec, b->d_desc, s1->dev, s1->n, (int)(j & 1),
+                                   persistent_ctas(s1->n), b->stream);
+            left -= 1;
+        }
+        if (e != cudaSuccess) return host_cuda_fail(e, "batched step kernel");
+        ++j;
+    }
+    *launches = j;
+    return RDC_OK;
+}
+
+int upload_desc(rdc_batch* b)
+{
+    if (b->n == 0) return RDC_OK;
+    if (b->d_desc_cap < b->n) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamSynchronize");
+        if (b->d_desc) cudaFree(b->d_desc);
+        b->d_desc = nullptr;
+        b->d_desc_cap = 0;
+        const int cap = std::max(16, 2 * b->n);
+        e = cudaMalloc((void**)&b->d_desc, sizeof(GridDesc) * cap);
+        if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(descriptors)");
+        b->d_desc_cap = cap;
+        free_graphs(b);  // graphs captured the old table's address
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), b->desc.size() * sizeof(GridDesc),
+                                    cudaMemcpyHostToDevice, b->stream);
+    return e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "cudaMemcpyAsync(descriptors)");
+}
+
+int ensure_stage(rdc_batch* b, size_t bytes)
+{
+    if (b->stage_bytes >= bytes) return RDC_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamSynchronize");
+    if (b->stage) cudaFree(b->stage);
+    b->stage = nullptr;
+    b->stage_bytes = 0;
+    e = cudaMalloc(&b->stage, bytes);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(stage)");
+    b->stage_bytes = bytes;
+    return RDC_OK;
+}
+
+// Allocates and initialises one grid in slot g (rest state of its phi map).
+int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const float* phi_host)
+{
+    const int prec = b->prec;
+    const int esz = state_bytes(prec), psz = phi_bytes(prec);
+    auto r256 = [](size_t x) { return (x + 255) / 256 * 256; };
+    const int64_t pitch = (grid.width + 63) / 64 * 64;
+    const size_t sp = r256((size_t)pitch * grid.height * esz);
+    const size_t total = 4 * sp + r256((size_t)pitch * grid.height * psz);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, total);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(batch grid)");
+    e = cudaMemsetAsync(mem, 0, total, b->stream);
+    GridDesc d;
+    std::memset(&d, 0, sizeof d);
+    unsigned char* q = (unsigned char*)mem;
+    d.u[0] = q;
+    d.u[1] = q + sp;
+    d.v[0] = q + 2 * sp;
+    d.v[1] = q + 3 * sp;
+    d.phi = q + 4 * sp;
+    d.W = grid.width;
+    d.H = grid.height;
+    d.pitch = pitch;
+    d.eps = p.eps;
+    d.f = p.f;
+    d.q = p.q;
+    d.Du = p.Du;
+    d.dt = p.dt;
+    d.inv_dx2 = 1.0 / (p.dx * p.dx);
+    d.par = 0;
+    if (e == cudaSuccess) {
+        if (phi_host) {
+            const size_t bytes = (size_t)grid.width * grid.height * sizeof(float);
+            int rc = ensure_stage(b, bytes);
+            if (rc) {
+                cudaFree(mem);
+                return rc;
+            }
+            e = cudaMemcpyAsync(b->stage, phi_host, bytes, cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess)
+                e = launch_phi_in(prec, 0, b->stage, (void*)d.phi, d.W, d.H, pitch, b->stream);
+        } else {
+            e = launch_fill_phi(prec, (void*)d.phi, d.W, d.H, pitch, kPhiActive, b->stream);
+        }
+    }
+    if (e == cudaSuccess)
+        e = launch_rest(prec, d.u[0], d.v[0], d.phi, d.W, d.H, pitch, p.f, p.q, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return host_cuda_fail(e, "batch grid initialisation");
+    }
+    b->grids[g] = grid;
+    b->params[g] = p;
+    b->desc[g] = d;
+    b->mem[g] = mem;
+    return RDC_OK;
+}
+
+bool grid_ok(const rdc_batch* b, rdc_grid grid, const rdc_params* p, const float* phi_host)
+{
+    if (grid.width < 1 || grid.height < 1 || !host_params_valid(p)) return false;
+    if (p->precision != b->prec || p->flags != 0) return false;
+    double mx = 0.0;
+    if (phi_host)
+        return host_scan_phi(phi_host, 0, (int64_t)grid.width * grid.height, p, &mx);
+    return host_phi_ok(kPhiActive, p);
+}
+
+bool subset_of(rdc_batch* b, const int32_t* idx, int32_t m, std::vector<int>* out)
+{
+    out->clear();
+    if (!idx) {
+        for (int g = 0; g < b->n; ++g)
+            if (b->mem[g]) out->push_back(g);
+        return true;
+    }
+    if (m < 0) return false;
+    for (int32_t i = 0; i < m; ++i) {
+        if (idx[i] < 0 || idx[i] >= b->n || !b->mem[idx[i]]) return false;
+        out->push_back(idx[i]);
+    }
+    std::sort(out->begin(), out->end());
+    return std::adjacent_find(out->begin(), out->end()) == out->end();
+}
+
+}  // namespace
+
+extern "C" {
+
+int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
+                     const float* const* phi_host, void* stream, rdc_batch** out)
+{
+    if (!out) return RDC_EINVAL;
+    *out = nullptr;
+    if (n < 0 || !params || (n > 0 && !grids)) return RDC_EINVAL;
+    if (!host_params_valid(&params[0]) || params[0].flags != 0) return RDC_EINVAL;
+    int rc = host_check_device();
+    if (rc) return rc;
+    rdc_batch* b = new (std::nothrow) rdc_batch();
+    if (!b) return RDC_ENOMEM;
+    b->prec = params[0].precision;
+    b->k_block = params[0].k_block;
+    b->cfg.k = b->k_block == 0 ? 1 : b->k_block;
+    for (int g = 0; g < n; ++g) {
+        if (params[g].k_block != b->k_block ||
+            !grid_ok(b, grids[g], &params[g], phi_host ? phi_host[g] : nullptr)) {
+            delete b;
+            return RDC_EINVAL;
+        }
+    }
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete b;
+            return host_cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        b->owns_stream = true;
+    }
+    cudaError_t e = cudaMalloc((void**)&b->d_flag, 256);
+    if (e != cudaSuccess) {
+        rdc_batch_destroy(b);
+        return host_cuda_fail(e, "cudaMalloc(flag)");
+    }
+    for (int g = 0; g < n; ++g) {
+        int32_t idx = -1;
+        rc = rdc_batch_add(b, grids[g], &params[g], phi_host ? phi_host[g] : nullptr, &idx);
+        if (rc) {
+            rdc_batch_destroy(b);
+            return rc;
+        }
+    }
+    *out = b;
+    return RDC_OK;
+}
+
+int rdc_batch_add(rdc_batch* b, rdc_grid grid, const rdc_params* p, const float* phi_host,
+                  int32_t* idx)
+{
+    if (!b || !idx || !p) return RDC_EINVAL;
+    *idx = -1;
+    if (p->k_block != b->k_block || !grid_ok(b, grid, p, phi_host)) return RDC_EINVAL;
+    int g = 0;
+    while (g < b->n && b->mem[g]) ++g;  // reuse a free slot
+    if (g == b->n) {
+        b->grids.push_back(grid);
+        b->params.push_back(*p);
+        b->desc.push_back(GridDesc{});
+        b->mem.push_back(nullptr);
+        b->n += 1;
+    }
+    int rc = init_slot(b, g, grid, *p, phi_host);
+    if (rc) return rc;
+    free_graphs(b);
+    free_items(b->step1_items);
+    free_items(b->stream_items);
+    *idx = g;
+    return RDC_OK;
+}
+
+int rdc_batch_remove(rdc_batch* b, int32_t idx)
+{
+    if (!b || idx < 0 || idx >= b->n || !b->mem[idx]) return RDC_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamSynchronize");
+    cudaFree(b->mem[idx]);
+    b->mem[idx] = nullptr;
+    std::memset(&b->desc[idx], 0, sizeof(GridDesc));
+    free_graphs(b);
+    free_items(b->step1_items);
+    free_items(b->stream_items);
+    return RDC_OK;
+}
+
+void rdc_batch_destroy(rdc_batch* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    free_graphs(b);
+    free_items(b->step1_items);
+    free_items(b->stream_items);
+    for (void* m : b->mem)
+        if (m) cudaFree(m);
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_flag) cudaFree(b->d_flag);
+    if (b->stage) cudaFree(b->stage);
+    if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int rdc_batch_seed(rdc_batch* b, int32_t idx, double cx, double cy, double r, double value)
+{
+    if (!b || idx < 0 || idx >= b->n || !b->mem[idx] || !std::isfinite(cx) || !std::isfinite(cy) ||
+        !std::isfinite(value) || !(r >= 0.0) || !(r < 16777216.0))
+        return RDC_EINVAL;
+    const GridDesc& d = b->desc[idx];
+    cudaError_t e = launch_seed(b->prec, d.u[d.par], d.W, d.H, d.pitch, cx, cy, r, value, b->stream);
+    return e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "seed kernel");
+}
+
+int rdc_batch_set_state(rdc_batch* b, int32_t idx, const void* u_host, const void* v_host,
+                        int32_t dtype)
+{
+    if (!b || idx < 0 || idx >= b->n || !b->mem[idx] || dtype < 0 || dtype > 3)
+        return RDC_EINVAL;
+    const GridDesc& d = b->desc[idx];
+    const int esz = state_bytes(b->prec);
+    const void* src[2] = {u_host, v_host};
+    void* dst[2] = {d.u[d.par], d.v[d.par]};
+    for (int k = 0; k < 2; ++k) {
+        if (!src[k]) continue;
+        cudaError_t e;
+        if (dtype == b->prec) {
+            e = cudaMemcpy2DAsync(dst[k], (size_t)d.pitch * esz, src[k], (size_t)d.W * esz,
+                                  (size_t)d.W * esz, d.H, cudaMemcpyHostToDevice, b->stream);
+        } else {
+            const size_t bytes = (size_t)d.W * d.H * dtype_bytes(dtype);
+            const int rc = ensure_stage(b, bytes);
+            if (rc) return rc;
+            e = cudaMemcpyAsync(b->stage, src[k], bytes, cudaMemcpyHostToDevice, b->stream);
+            if (e == cudaSuccess)
+                e = launch_pack_in(b->prec, dtype, b->stage, dst[k], d.W, d.H, d.pitch, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        }
+        if (e != cudaSuccess) return host_cuda_fail(e, "rdc_batch_set_state");
+    }
+    return RDC_OK;
+}
+
+int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n)
+{
+    if (!b || n < 0) return RDC_EINVAL;
+    std::vector<int> subset;
+    if (!subset_of(b, idx, m, &subset)) return RDC_EINVAL;
+    if (subset.empty() || n == 0) return RDC_OK;
+    for (int g = 0; g < b->n; ++g) b->desc[g].active = 0;
+    for (int g : subset) b->desc[g].active = 1;
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    // build the work lists outside any capture (they allocate)
+    ItemList* tmp = nullptr;
+    if ((rc = get_items(b, false, &tmp))) return rc;
+    if (b->cfg.k > 1 && (rc = get_items(b, true, &tmp))) return rc;
+    int64_t L = 0;
+    if (b->use_graphs) {
+        const std::vector<int64_t> key{n, b->cfg.k, b->cfg.rows, b->cfg.krows};
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamBeginCapture");
+            rc = enqueue_sequence(b, n, &L);
+            e = cudaStreamEndCapture(b->stream, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamEndCapture");
+            GraphEntry ge;
+            e = cudaGraphInstantiate(&ge.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return host_cuda_fail(e, "cudaGraphInstantiate");
+            ge.launches = L;
+            if (b->graphs.size() >= 64) free_graphs(b);
+            it = b->graphs.emplace(key, ge).first;
+        }
+        cudaError_t e = cudaGraphLaunch(it->second.exec, b->stream);
+        if (e != cudaSuccess) return host_cuda_fail(e, "cudaGraphLaunch");
+        L = it->second.launches;
+        b->graph_launches += 1;
+    } else {
+        rc = enqueue_sequence(b, n, &L);
+        if (rc) return rc;
+    }
+    for (int g : subset) {
+        b->desc[g].par = (int)((b->desc[g].par + L) & 1);
+        b->cells_stepped += (double)b->grids[g].width * b->grids[g].height * (double)n;
+    }
+    b->launches += L;
+    return RDC_OK;
+}
+
+int rdc_batch_check(rdc_batch* b, int32_t idx, int64_t* first_bad)
+{
+    if (!b || idx < 0 || idx >= b->n || !b->mem[idx]) return RDC_EINVAL;
+    const GridDesc& d = b->desc[idx];
+    cudaError_t e = cudaMemsetAsync(b->d_flag, 0xFF, sizeof(unsigned long long), b->stream);
+    if (e == cudaSuccess)
+        e = launch_health(b->prec, d.u[d.par], d.W, d.H, d.pitch, b->params[idx].q, b->d_flag,
+                          b->stream);
+    unsigned long long h = ~0ull;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h, b->d_flag, sizeof h, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return host_cuda_fail(e, "batch health check");
+    if (first_bad) *first_bad = (h == ~0ull) ? -1 : (int64_t)h;
+    return h == ~0ull ? RDC_OK : RDC_ENONFINITE;
+}
+
+int rdc_batch_read(rdc_batch* b, int32_t idx, void* u_out, void* v_out, int32_t dtype)
+{
+    if (!b || idx < 0 || idx >= b->n || !b->mem[idx] || dtype < 0 || dtype > 3)
+        return RDC_EINVAL;
+    const GridDesc& d = b->desc[idx];
+    const int esz = state_bytes(b->prec);
+    const void* src[2] = {d.u[d.par], d.v[d.par]};
+    void* dst[2] = {u_out, v_out};
+    for (int k = 0; k < 2; ++k) {
+        if (!dst[k]) continue;
+        cudaError_t e;
+        if (dtype == b->prec) {
+            e = cudaMemcpy2DAsync(dst[k], (size_t)d.W * esz, src[k], (size_t)d.pitch * esz,
+                                  (size_t)d.W * esz, d.H, cudaMemcpyDeviceToHost, b->stream);
+        } else {
+            const size_t bytes = (size_t)d.W * d.H * dtype_bytes(dtype);
+            const int rc = ensure_stage(b, bytes);
+            if (rc) return rc;
+            e = launch_pack_out(b->prec, dtype, src[k], b->stage, d.W, d.H, d.pitch, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(dst[k], b->stage, bytes, cudaMemcpyDeviceToHost, b->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return host_cuda_fail(e, "rdc_batch_read");
+    }
+    return rdc_batch_check(b, idx, nullptr);
+}
+
+int rdc_batch_sync(rdc_batch* b)
+{
+    if (!b) return RDC_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "cudaStreamSynchronize");
+}
+
+int rdc_batch_set_config(rdc_batch* b, int32_t k, int32_t rows, int32_t krows, int32_t graphs)
+{
+    if (!b || k < 1 || k > 8 || rows < 1 || krows < 1 || graphs < 0 || graphs > 1)
+        return RDC_EINVAL;
+    cudaStreamSynchronize(b->stream);
+    free_graphs(b);
+    if (rows != b->cfg.rows) free_items(b->step1_items);
+    if (krows != b->cfg.krows || k != b->cfg.k) free_items(b->stream_items);
+    b->cfg.k = k;
+    b->cfg.rows = rows;
+    b->cfg.krows = krows;
+    b->use_graphs = graphs != 0;
+    return RDC_OK;
+}
+
+int rdc_batch_get_info(rdc_batch* b, rdc_batch_info* out)
+{
+    if (!b || !out) return RDC_EINVAL;
+    std::memset(out, 0, sizeof *out);
+    int live = 0;
+    for (void* m : b->mem) live += m ? 1 : 0;
+    out->ngrids = live;
+    out->slots = b->n;
+    out->precision = b->prec;
+    out->k = b->cfg.k;
+    out->rows = b->cfg.rows;
+    out->krows = b->cfg.krows;
+    out->graphs = b->use_graphs ? 1 : 0;
+    double cells = 0;
+    for (int g = 0; g < b->n; ++g)
+        if (b->mem[g]) cells += (double)b->grids[g].width * b->grids[g].height;
+    out->total_cells = cells;
+    out->launches = b->launches;
+    out->graph_launches = b->graph_launches;
+    out->cells_stepped = b->cells_stepped;
+    out->stream = (void*)b->stream;
+    return RDC_OK;
+}
+
+int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
+{
+    if (!b || reps < 1) return RDC_EINVAL;
+    double cells = 0;
+    for (int g = 0; g < b->n; ++g) {
+        b->desc[g].active = b->mem[g] ? 1 : 0;
+        if (b->mem[g]) cells += (double)b->grids[g].width * b->grids[g].height;
+    }
+    if (cells == 0) return RDC_EINVAL;
+    int rc = upload_desc(b);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return RDC_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return RDC_ECUDA;
+    }
+    const Config saved = b->cfg;
+    Config best = saved;
+    double best_rate = -1.0;
+    struct Cand { int k, rows, krows; };
+    std::vector<Cand> cands;
+    for (int rows : {8, 16, 32}) cands.push_back({1, rows, saved.krows});
+    for (int k : {2, 3, 4, 6, 8})
+        for (int krows : {32, 64, 128, 256}) cands.push_back({k, saved.rows, krows});
+    for (const Cand& c : cands) {
+        b->cfg.k = c.k;
+        b->cfg.rows = c.rows;
+        b->cfg.krows = c.krows;
+        free_items(b->step1_items);
+        free_items(b->stream_items);
+        ItemList* L = nullptr;
+        rc = get_items(b, c.k > 1, &L);
+        if (rc) break;
+        // Every timed launch reads the current buffers (j = 0) and writes the
+        // spare ones, so tuning never advances the state.
+        auto launch = [&]() {
+            return c.k > 1 ? launch_batch_stream(b->prec, b->d_desc, L->dev, L->n, c.k, 0,
+                                                 persistent_ctas(L->n), b->stream)
+                           : launch_batch_step1(b->prec, b->d_desc, L->dev, L->n, 0,
+                                                persistent_ctas(L->n), b->stream);
+        };
+        cudaError_t e = launch();  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = host_cuda_fail(e, "autotune launch");
+            break;
+        }
+        const double rate = cells * c.k * reps / (ms * 1e-3);
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = b->cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    free_items(b->step1_items);
+    free_items(b->stream_items);
+    free_graphs(b);
+    b->cfg = rc ? saved : best;
+    if (rc) return rc;
+    if (out) {
+        rdc_batch_get_info(b, out);
+        out->tuned_gcups = best_rate / 1e9;
+    }
+    return RDC_OK;
+}
+
+}  // extern "C"

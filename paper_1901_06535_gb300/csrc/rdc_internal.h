@@ -14,6 +14,9 @@ struct ModelD {
     double eps, f, q, Du, dt, inv_dx2;
 };
 
+// Which terms of u_t a step evaluates (match the RDC_*_ONLY flags).
+enum { MODE_FULL = 0, MODE_DIFFUSION = 1, MODE_REACTION = 2 };
+
 // Storage codes (match RDC_F32 ... RDC_F32_F16STORE).
 enum Prec { P_F32 = 0, P_F64 = 1, P_BF16 = 2, P_F16 = 3 };
 
@@ -25,10 +28,14 @@ struct Shape1 {
     int rows;
 };
 
-// Tile of the temporally blocked kernel: tx x ty interior cells per CTA,
-// k Euler steps per launch (1..8), nthreads threads (a multiple of 32).
+// Temporal blocking, k Euler steps per launch (1..8).  variant 0: the
+// register-streamed kernel (full model only), each CTA marching `krows` rows;
+// variant 1: the shared-memory tile kernel with tx x ty interior cells and
+// nthreads threads (a multiple of 32).
 struct ShapeK {
     int tx, ty, k, nthreads;
+    int variant = 0;
+    int krows = 256;
 };
 
 // Geometry of one grid's planes.  All planes share the row pitch `pitch`
@@ -43,12 +50,50 @@ struct Planes {
     int64_t pitch;
 };
 
+// One grid of a batch, as the batched kernels read it from device memory.
+// par is the index (0/1) of the current buffer when the batch launch
+// sequence starts; launch j of a sequence reads buffer (par + j) & 1 and
+// writes the other.  Grids with active == 0 are skipped by every launch of
+// the sequence, so one work list (and one captured graph) serves any subset.  Model constants stay FP64 here and are rounded to the
+// compute precision per work item, exactly as the single-grid launchers do.
+struct GridDesc {
+    void* u[2];
+    void* v[2];
+    const void* phi;
+    int W, H;
+    long long pitch;  // elements, all planes
+    double eps, f, q, Du, dt, inv_dx2;
+    int par;
+    int active;  // 0: this call leaves the grid alone (its items are skipped)
+};
+
+// A work item of a batched launch: one warp's strip of one grid.
+//   single step : columns [x0, x0 + 32 * VEC), rows [y0, y1)
+//   streamed k  : output columns [x0, x0 + OUTC), rows [y0, y1)
+struct Item {
+    int g, x0, y0, y1;
+};
+
 // Kernels of rdc_step_*.cu.
 cudaError_t launch_step1(int prec, int mode, const Planes& g, const ModelD& m,
                          Shape1 s, cudaStream_t st);
 cudaError_t launch_stepk(int prec, int mode, const Planes& g, const ModelD& m,
                          ShapeK s, cudaStream_t st);
 size_t stepk_smem_bytes(int prec, ShapeK s);
+cudaError_t launch_stream(int prec, const Planes& g, const ModelD& m, int k, int rows,
+                          cudaStream_t st);
+// Batched launches over a device item list (persistent: `ctas` CTAs of 128
+// threads, each warp looping over items); launch index j selects buffers.
+cudaError_t launch_batch_step1(int prec, const GridDesc* d, const Item* items, int nitems,
+                               int j, int ctas, cudaStream_t st);
+cudaError_t launch_batch_stream(int prec, const GridDesc* d, const Item* items, int nitems,
+                                int k, int j, int ctas, cudaStream_t st);
+// Columns a warp covers (single step) / writes (streamed, k steps).
+int batch_step1_cols(int prec);
+int batch_stream_outc(int prec, int k);
+// The kernel that rdc_step uses for one launch of k > 1 steps.
+cudaError_t launch_kblock(int prec, int mode, const Planes& g, const ModelD& m,
+                          ShapeK s, cudaStream_t st);
 
 // Kernels of rdc_aux.cu.
 cudaError_t launch_rest(int prec, void* u, void* v, const void* phi, int W,
@@ -71,6 +116,9 @@ cudaError_t launch_pack_out(int prec, int dst_dtype, const void* src, void* dst,
 // phi: packed float/double host-order -> pitched phi plane of `prec`.
 cudaError_t launch_phi_in(int prec, int src_dtype, const void* src, void* dst,
                           int W, int H, int64_t pitch, cudaStream_t st);
+// phi plane := value (uniform map).
+cudaError_t launch_fill_phi(int prec, void* dst, int W, int H, int64_t pitch, double value,
+                            cudaStream_t st);
 // u at flat cell indices -> doubles.
 cudaError_t launch_probe(int prec, const void* u, int W, int64_t pitch,
                          const int64_t* cells, int n, double* out,

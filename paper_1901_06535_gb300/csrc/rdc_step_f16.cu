@@ -1,5 +1,6 @@
 // Step kernels instantiated for __half storage of u and v.
 #include "rdc_step_impl.cuh"
+#include "rdc_stream_impl.cuh"
 
 namespace rdc {
 
@@ -14,5 +15,24 @@ cudaError_t launch_stepk_f16(int mode, const Planes& g, const ModelD& m, ShapeK 
 }
 
 size_t stepk_smem_f16(ShapeK s) { return stepk_smem_t<__half>(s); }
+
+cudaError_t launch_stream_f16(const Planes& g, const ModelD& m, int k, int rows, cudaStream_t st)
+{
+    return launch_stream_t<__half>(g, m, k, rows, st);
+}
+
+cudaError_t launch_batch_step1_f16(const GridDesc* d, const Item* items, int nitems, int j,
+                                  int ctas, cudaStream_t st)
+{
+    return launch_batch_step1_t<__half>(d, items, nitems, j, ctas, st);
+}
+
+cudaError_t launch_batch_stream_f16(const GridDesc* d, const Item* items, int nitems, int k,
+                                   int j, int ctas, cudaStream_t st)
+{
+    return launch_batch_stream_t<__half>(d, items, nitems, k, j, ctas, st);
+}
+
+int batch_stream_outc_f16(int k) { return stream_outc_t<__half>(k); }
 
 }  // namespace rdc

@@ -1,5 +1,6 @@
 // Step kernels instantiated for double storage of u and v.
 #include "rdc_step_impl.cuh"
+#include "rdc_stream_impl.cuh"
 
 namespace rdc {
 
@@ -14,5 +15,24 @@ cudaError_t launch_stepk_f64(int mode, const Planes& g, const ModelD& m, ShapeK 
 }
 
 size_t stepk_smem_f64(ShapeK s) { return stepk_smem_t<double>(s); }
+
+cudaError_t launch_stream_f64(const Planes& g, const ModelD& m, int k, int rows, cudaStream_t st)
+{
+    return launch_stream_t<double>(g, m, k, rows, st);
+}
+
+cudaError_t launch_batch_step1_f64(const GridDesc* d, const Item* items, int nitems, int j,
+                                  int ctas, cudaStream_t st)
+{
+    return launch_batch_step1_t<double>(d, items, nitems, j, ctas, st);
+}
+
+cudaError_t launch_batch_stream_f64(const GridDesc* d, const Item* items, int nitems, int k,
+                                   int j, int ctas, cudaStream_t st)
+{
+    return launch_batch_stream_t<double>(d, items, nitems, k, j, ctas, st);
+}
+
+int batch_stream_outc_f64(int k) { return stream_outc_t<double>(k); }
 
 }  // namespace rdc

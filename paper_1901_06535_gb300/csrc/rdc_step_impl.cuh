@@ -23,19 +23,21 @@
 
 namespace rdc {
 
+// One warp's share of a single Euler step: 32 vectors of VEC cells starting
+// at column wcol0, rows [row0, row1).  Warps are independent (no shared
+// memory, no block barrier), so the same body serves one grid per launch
+// (k_step1) and a work list over many grids (k_step1_batch).
 template <typename S, int MODE>
-__global__ void __launch_bounds__(256)
-k_step1(const S* __restrict__ u, const S* __restrict__ v,
-        const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
-        S* __restrict__ v1, int W, int H, int64_t pitch, int rows,
-        Model<typename Traits<S>::T> m)
+__device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __restrict__ v,
+                                           const typename Traits<S>::PhiT* __restrict__ phi,
+                                           S* __restrict__ u1, S* __restrict__ v1, int W,
+                                           int H, int64_t pitch, int wcol0, int row0,
+                                           int row1, const Model<typename Traits<S>::T>& m)
 {
     using T = typename Traits<S>::T;
     constexpr int VEC = Traits<S>::VEC;
     const int lane = threadIdx.x & 31;
-    const int col0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
-    const int row0 = blockIdx.y * rows;
-    const int row1 = min(row0 + rows, H);
+    const int col0 = wcol0 + lane * VEC;
     const bool act = col0 < W;
 
     T un[VEC], uc[VEC], us[VEC], vv[VEC], ph[VEC];
@@ -89,6 +91,65 @@ k_step1(const S* __restrict__ u, const S* __restrict__ v,
             uc[e] = us[e];
         }
     }
+}
+
+template <typename S, int MODE>
+__global__ void __launch_bounds__(256)
+k_step1(const S* __restrict__ u, const S* __restrict__ v,
+        const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
+        S* __restrict__ v1, int W, int H, int64_t pitch, int rows,
+        Model<typename Traits<S>::T> m)
+{
+    constexpr int VEC = Traits<S>::VEC;
+    const int wcol0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * VEC;
+    const int row0 = blockIdx.y * rows;
+    step1_warp<S, MODE>(u, v, phi, u1, v1, W, H, pitch, wcol0, row0, min(row0 + rows, H), m);
+}
+
+template <typename T>
+__device__ __forceinline__ Model<T> model_of(const GridDesc& d)
+{
+    Model<T> m;
+    m.eps = (T)d.eps;
+    m.f = (T)d.f;
+    m.q = (T)d.q;
+    m.Du = (T)d.Du;
+    m.dt = (T)d.dt;
+    m.inv_dx2 = (T)d.inv_dx2;
+    m.inv_eps = (T)(1.0 / d.eps);
+    return m;
+}
+
+// Persistent single step over a batch of grids: every warp takes items
+// w, w + (all warps), ...; each item is one warp's strip of one grid.
+template <typename S>
+__global__ void __launch_bounds__(128)
+k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
+              int j)
+{
+    using T = typename Traits<S>::T;
+    using PhiT = typename Traits<S>::PhiT;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
+        const Item item = items[it];
+        const GridDesc& d = descs[item.g];
+        if (!d.active) continue;
+        const int par = (d.par + j) & 1;
+        step1_warp<S, MODE_FULL>(static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
+                                 static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
+                                 static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0,
+                                 item.y0, item.y1, model_of<T>(d));
+    }
+}
+
+template <typename S>
+cudaError_t launch_batch_step1_t(const GridDesc* d, const Item* items, int nitems, int j,
+                                 int ctas, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (ctas < 1) return cudaErrorInvalidValue;
+    k_step1_batch<S><<<ctas, 128, 0, st>>>(d, items, nitems, j);
+    return cudaGetLastError();
 }
 
 // Shared-memory layout of k_stepk: four planes of (tx+2k) x (ty+2k) compute
@@ -183,6 +244,7 @@ Model<typename Traits<S>::T> make_model(const ModelD& d)
     m.Du = (T)d.Du;
     m.dt = (T)d.dt;
     m.inv_dx2 = (T)d.inv_dx2;
+    m.inv_eps = (T)(1.0 / d.eps);
     return m;
 }
 

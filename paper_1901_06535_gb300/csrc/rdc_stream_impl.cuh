@@ -1,0 +1,351 @@
+// k_stepk_stream: K explicit Euler steps of Eq. 1 per launch (temporal
+// blocking) with every intermediate time level held in registers.
+//
+// Each warp owns a strip of 32 * VEC columns (one VEC-cell vector per lane)
+// and marches down a chunk of rows.  At iteration t it loads row t of u, v
+// (time level 0) and, for l = 1..K, computes row t - l of time level l from
+// rows t-l-1, t-l, t-l+1 of level l-1 -- a wavefront in (row, time).  Each
+// level keeps the last three u rows and two v rows it produced in registers;
+// only level K is written to memory.  East/west neighbours come from the
+// adjacent lanes by shuffles, so a level is valid one column less on each side
+// than the level before: warps overlap by HALO = roundup(K, VEC) columns per
+// side (a multiple of VEC keeps every vector 16/8-byte aligned) and each
+// writes only its 32 * VEC - 2 * HALO interior columns.  Chunks overlap by K
+// rows above and below for the same reason.  At the grid's own borders the
+// mirror rule needs no outside data, so those cells are valid at every level.
+//
+// Per cell and level this does exactly what k_step1 does (same cell_update,
+// same rounding to the storage type), so K steps here equal K launches of
+// k_step1 bit for bit.  HBM traffic is that of one step per K steps (plus the
+// halo overlap); the rest is FP32 (or FP64) arithmetic.
+#pragma once
+
+#include "rdc_device.cuh"
+#include "rdc_internal.h"
+
+namespace rdc {
+
+// N consecutive stored values (N * sizeof(S) = 4, 8 or 16 bytes) -> compute
+// type (S may also be a phi type: float or double).
+template <typename S>
+struct Widened { using T = typename Traits<S>::T; };
+
+template <typename S, int N>
+struct VecN {
+    using T = typename Widened<S>::T;
+    static constexpr int BYTES = N * (int)sizeof(S);
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "vector of 4, 8 or 16 bytes");
+    union Raw {
+        uint4 q;
+        uint2 d;
+        unsigned int w;
+        S s[N];
+    };
+    static __device__ __forceinline__ void load(const S* p, T (&o)[N])
+    {
+        Raw r;
+        if constexpr (BYTES == 16) r.q = __ldg(reinterpret_cast<const uint4*>(p));
+        else if constexpr (BYTES == 8) r.d = __ldg(reinterpret_cast<const uint2*>(p));
+        else r.w = __ldg(reinterpret_cast<const unsigned int*>(p));
+#pragma unroll
+        for (int e = 0; e < N; ++e) o[e] = widen(r.s[e]);
+    }
+    static __device__ __forceinline__ void store(S* p, const T (&x)[N])
+    {
+        Raw r;
+#pragma unroll
+        for (int e = 0; e < N; ++e) r.s[e] = narrow<S>(x[e]);
+        if constexpr (BYTES == 16) *reinterpret_cast<uint4*>(p) = r.q;
+        else if constexpr (BYTES == 8) *reinterpret_cast<uint2*>(p) = r.d;
+        else *reinterpret_cast<unsigned int*>(p) = r.w;
+    }
+};
+
+template <typename S, int K, int N>
+struct StreamGeom {
+    static constexpr int HALO = (K + N - 1) / N * N;  // overlap per side, columns
+    static constexpr int WCOLS = 32 * N;              // columns a warp holds
+    static constexpr int OUTC = WCOLS - 2 * HALO;     // columns a warp writes
+    static_assert(OUTC > 0, "halo wider than the warp");
+};
+
+// One warp's share: output columns [col_out, col_out + OUTC), output rows
+// [y0, y1).  Warps are independent, so the same body serves one grid per
+// launch (k_stepk_stream) and a work list over many grids (k_stream_batch).
+//
+// Borders.  Rows: when a level produces row 0 it also writes that row into
+// its "row -1" register (the mirror ghost), and when it passes row H-1 it
+// produces a ghost row H equal to row H-1; the next level then reads its
+// north/south neighbours without any per-cell test.  Columns: only a warp
+// whose strip touches column 0 or W-1 (XE) tests columns per cell.
+template <typename S, int MODE, int K, int N, bool XE>
+__device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
+                                                 const S* __restrict__ v,
+                                                 const typename Traits<S>::PhiT* __restrict__ phi,
+                                                 S* __restrict__ u1, S* __restrict__ v1, int W,
+                                                 int H, int64_t pitch, int col_out, int y0,
+                                                 int y1, const Model<typename Traits<S>::T>& m)
+{
+    using T = typename Traits<S>::T;
+    using G = StreamGeom<S, K, N>;
+    const int lane = threadIdx.x & 31;
+    const int a = col_out - G::HALO;                  // first column the warp holds
+    const int cl = a + lane * N;                      // first column of this lane
+    const bool in_grid = (cl >= 0) && (cl < W);       // vectors never straddle column 0
+    const int t0 = max(y0 - K, 0);
+    const int t_end = y1 - 1 + K;                     // level K reaches row y1 - 1 here
+
+    // P*[l]: last three u rows of level l (P2 oldest); Q*[l]: last two v rows.
+    T P0[K][N], P1[K][N], P2[K][N], Q0[K][N], Q1[K][N];
+#pragma unroll
+    for (int l = 0; l < K; ++l)
+#pragma unroll
+        for (int e = 0; e < N; ++e) P0[l][e] = P1[l][e] = P2[l][e] = Q0[l][e] = Q1[l][e] = T(0);
+
+    for (int t = t0; t <= t_end; ++t) {
+        // level 0: load row t (row H is the ghost copy of row H - 1)
+        {
+            T nu[N], nv[N];
+#pragma unroll
+            for (int e = 0; e < N; ++e) nu[e] = nv[e] = T(0);
+            if (t < H) {
+                if (in_grid) {
+                    const int64_t o = (int64_t)t * pitch + cl;
+                    VecN<S, N>::load(u + o, nu);
+                    VecN<S, N>::load(v + o, nv);
+                }
+            } else if (t == H) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) nu[e] = P0[0][e];
+            }
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+                P2[0][e] = P1[0][e];
+                P1[0][e] = P0[0][e];
+                P0[0][e] = nu[e];
+                Q1[0][e] = Q0[0][e];
+                Q0[0][e] = nv[e];
+            }
+            if (t == 0) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) P1[0][e] = P0[0][e];  // ghost row -1
+            }
+        }
+        // levels 1..K: row r = t - l from rows r-1, r, r+1 of level l-1
+#pragma unroll
+        for (int l = 1; l <= K; ++l) {
+            const int r = t - l;
+            const bool live = (r >= 0) && (r < H);   // warp-uniform
+            T nu[N], nv[N];
+            const T wsh = __shfl_up_sync(0xffffffffu, P1[l - 1][N - 1], 1);
+            const T esh = __shfl_down_sync(0xffffffffu, P1[l - 1][0], 1);
+            if (live) {
+                T ph[N];
+                if (in_grid) {
+                    VecN<typename Traits<S>::PhiT, N>::load(phi + (int64_t)r * pitch + cl, ph);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < N; ++e) ph[e] = T(0);
+                }
+#pragma unroll
+                for (int e = 0; e < N; ++e) {
+                    const T c = P1[l - 1][e];
+                    T w = (e == 0) ? wsh : P1[l - 1][e - 1];
+                    T ea = (e == N - 1) ? esh : P1[l - 1][e + 1];
+                    if (XE) {
+                        const int col = cl + e;
+                        if (col <= 0) w = c;          // mirror at the west border
+                        if (col >= W - 1) ea = c;     // mirror at the east border
+                    }
+                    T un, vn;
+                    cell_update<MODE>(c, w, ea, P2[l - 1][e], P0[l - 1][e], Q1[l - 1][e], ph[e],
+                                      m, un, vn);
+                    nu[e] = quantize<S>(un);
+                    nv[e] = quantize<S>(vn);
+                }
+            } else if (r == H && l < K) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) {   // ghost row H of level l
+                    nu[e] = P0[l][e];
+                    nv[e] = T(0);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < N; ++e) nu[e] = nv[e] = T(0);
+            }
+            if (l < K) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) {
+                    P2[l][e] = P1[l][e];
+                    P1[l][e] = P0[l][e];
+                    P0[l][e] = nu[e];
+                    Q1[l][e] = Q0[l][e];
+                    Q0[l][e] = nv[e];
+                }
+                if (r == 0) {
+#pragma unroll
+                    for (int e = 0; e < N; ++e) P1[l][e] = P0[l][e];  // ghost row -1
+                }
+            } else if (live && r >= y0 && r < y1) {
+                // level K: write this lane's vector if it lies in the warp's
+                // interior columns and inside the grid
+                if (cl >= col_out && cl < col_out + G::OUTC && cl < W) {
+                    const int64_t o = (int64_t)r * pitch + cl;
+                    if (cl + N <= W) {
+                        VecN<S, N>::store(u1 + o, nu);
+                        VecN<S, N>::store(v1 + o, nv);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < N; ++e)
+                            if (cl + e < W) {
+                                u1[o + e] = narrow<S>(nu[e]);
+                                v1[o + e] = narrow<S>(nv[e]);
+                            }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <typename S, int MODE, int K, int N>
+__device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __restrict__ v,
+                                            const typename Traits<S>::PhiT* __restrict__ phi,
+                                            S* __restrict__ u1, S* __restrict__ v1, int W,
+                                            int H, int64_t pitch, int col_out, int y0, int y1,
+                                            const Model<typename Traits<S>::T>& m)
+{
+    using G = StreamGeom<S, K, N>;
+    const int a = col_out - G::HALO;
+    const bool edge = (a <= 0) || (a + G::WCOLS - 1 >= W - 1);   // warp-uniform
+    if (edge)
+        stream_warp_impl<S, MODE, K, N, true>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
+    else
+        stream_warp_impl<S, MODE, K, N, false>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
+}
+
+template <typename S, int MODE, int K, int N>
+__global__ void __launch_bounds__(128)
+k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
+               const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
+               S* __restrict__ v1, int W, int H, int64_t pitch, int rows, int nwarps_x,
+               Model<typename Traits<S>::T> m)
+{
+    using G = StreamGeom<S, K, N>;
+    const int wx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (wx >= nwarps_x) return;                       // whole warps only
+    const int y0 = blockIdx.y * rows;
+    stream_warp<S, MODE, K, N>(u, v, phi, u1, v1, W, H, pitch, wx * G::OUTC, y0,
+                               min(y0 + rows, H), m);
+}
+
+// Persistent k-step launch over a batch of grids (see k_step1_batch).
+template <typename S, int K, int N>
+__global__ void __launch_bounds__(128)
+k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
+               int j)
+{
+    using T = typename Traits<S>::T;
+    using PhiT = typename Traits<S>::PhiT;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
+        const Item item = items[it];
+        const GridDesc& d = descs[item.g];
+        if (!d.active) continue;
+        const int par = (d.par + j) & 1;
+        stream_warp<S, MODE_FULL, K, N>(
+            static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
+            static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
+            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0, item.y0, item.y1,
+            model_of<T>(d));
+    }
+}
+
+// Cells per lane.  FP32: 4 (16-byte vectors) while the K levels' registers
+// fit (K <= 4), 2 beyond (more halo columns, fewer registers).  16-bit
+// storage: 4 (8-byte u, v vectors; the FP32 phi vector is 16 bytes).  FP64: 1.
+template <typename S, int K>
+struct StreamVec {
+    static constexpr int N = (sizeof(S) == 8) ? 1 : (sizeof(S) == 2 ? 4 : (K <= 4 ? 4 : 2));
+};
+
+template <typename S, int K>
+cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>& m, int rows,
+                            cudaStream_t st)
+{
+    using PhiT = typename Traits<S>::PhiT;
+    constexpr int N = StreamVec<S, K>::N;
+    using G = StreamGeom<S, K, N>;
+    const int nwx = (g.W + G::OUTC - 1) / G::OUTC;
+    const int wpb = 4;
+    if ((g.H + rows - 1) / rows > 65535) return cudaErrorInvalidValue;
+    dim3 grid((nwx + wpb - 1) / wpb, (g.H + rows - 1) / rows);
+    k_stepk_stream<S, MODE_FULL, K, N><<<grid, 32 * wpb, 0, st>>>(
+        static_cast<const S*>(g.u), static_cast<const S*>(g.v),
+        static_cast<const PhiT*>(g.phi), static_cast<S*>(g.u1), static_cast<S*>(g.v1), g.W,
+        g.H, g.pitch, rows, nwx, m);
+    return cudaGetLastError();
+}
+
+template <typename S, int K>
+cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nitems, int j,
+                                  int ctas, cudaStream_t st)
+{
+    constexpr int N = StreamVec<S, K>::N;
+    k_stream_batch<S, K, N><<<ctas, 128, 0, st>>>(d, items, nitems, j);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_batch_stream_t(const GridDesc* d, const Item* items, int nitems, int k,
+                                  int j, int ctas, cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    if (ctas < 1) return cudaErrorInvalidValue;
+    switch (k) {
+        case 2: return launch_stream_batch_k<S, 2>(d, items, nitems, j, ctas, st);
+        case 3: return launch_stream_batch_k<S, 3>(d, items, nitems, j, ctas, st);
+        case 4: return launch_stream_batch_k<S, 4>(d, items, nitems, j, ctas, st);
+        case 5: return launch_stream_batch_k<S, 5>(d, items, nitems, j, ctas, st);
+        case 6: return launch_stream_batch_k<S, 6>(d, items, nitems, j, ctas, st);
+        case 7: return launch_stream_batch_k<S, 7>(d, items, nitems, j, ctas, st);
+        case 8: return launch_stream_batch_k<S, 8>(d, items, nitems, j, ctas, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Output columns per warp of the streamed kernel.
+template <typename S>
+int stream_outc_t(int k)
+{
+    switch (k) {
+        case 2: return StreamGeom<S, 2, StreamVec<S, 2>::N>::OUTC;
+        case 3: return StreamGeom<S, 3, StreamVec<S, 3>::N>::OUTC;
+        case 4: return StreamGeom<S, 4, StreamVec<S, 4>::N>::OUTC;
+        case 5: return StreamGeom<S, 5, StreamVec<S, 5>::N>::OUTC;
+        case 6: return StreamGeom<S, 6, StreamVec<S, 6>::N>::OUTC;
+        case 7: return StreamGeom<S, 7, StreamVec<S, 7>::N>::OUTC;
+        case 8: return StreamGeom<S, 8, StreamVec<S, 8>::N>::OUTC;
+    }
+    return 0;
+}
+
+template <typename S>
+cudaError_t launch_stream_t(const Planes& g, const ModelD& md, int k, int rows,
+                            cudaStream_t st)
+{
+    if (rows < 1) return cudaErrorInvalidValue;
+    auto m = make_model<S>(md);
+    switch (k) {
+        case 2: return launch_stream_k<S, 2>(g, m, rows, st);
+        case 3: return launch_stream_k<S, 3>(g, m, rows, st);
+        case 4: return launch_stream_k<S, 4>(g, m, rows, st);
+        case 5: return launch_stream_k<S, 5>(g, m, rows, st);
+        case 6: return launch_stream_k<S, 6>(g, m, rows, st);
+        case 7: return launch_stream_k<S, 7>(g, m, rows, st);
+        case 8: return launch_stream_k<S, 8>(g, m, rows, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace rdc

@@ -1,0 +1,221 @@
+"""Interactive serving loop with continuous batching.
+
+Many interactive sessions (one grid each, as a user of the paper's app would
+have on a tablet, §3) share one GPU.  Each session asks for frames: apply a
+touch (catalytic stimulation, §2), then advance ``steps_per_frame`` Euler
+steps (the paper's "render rate", §2).  The server
+
+  * keeps every admitted session's state on the device (a rdc_batch slot);
+  * admits waiting sessions whenever the device-memory budget and the session
+    slots allow, and frees a session's memory when it leaves;
+  * every tick gathers all sessions that have a pending frame and no frame in
+    flight, applies their touches and advances all of them with one batched
+    launch sequence (a session arriving while others are on the GPU joins the
+    next tick, so its work overlaps theirs on the device);
+  * detects completion with CUDA events and records each frame's latency from
+    request to completion.
+
+All arithmetic runs in librdc; this module only schedules.  A session's
+result is bit-identical to running it alone (tests/test_gpu_serve.py).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import _capi as C
+
+
+@dataclasses.dataclass
+class Session:
+    sid: int
+    width: int
+    height: int
+    phi: np.ndarray | None = None          # H x W float32 map, or None (uniform)
+    eps: float | None = None
+    frames: int = 10                        # frames the session will request
+    touches: list = dataclasses.field(default_factory=list)  # per frame (cx, cy, r, value) or None
+    # filled in by the server
+    slot: int = -1
+    done_frames: int = 0
+    arrival: float = 0.0
+    admitted_at: float = 0.0
+
+    def state_bytes(self, precision: int) -> int:
+        esz = {C.RDC_F32: 4, C.RDC_F64: 8}.get(precision, 2)
+        psz = 8 if precision == C.RDC_F64 else 4
+        pitch = (self.width + 63) // 64 * 64
+        return pitch * self.height * (4 * esz + psz)
+
+
+@dataclasses.dataclass
+class Frame:
+    sid: int
+    index: int
+    requested: float
+    completed: float = 0.0
+
+    @property
+    def latency(self) -> float:
+        return self.completed - self.requested
+
+
+class Server:
+    def __init__(self, precision=C.RDC_F32, k_block: int = 2, steps_per_frame: int = 50,
+                 memory_budget: int | None = None, max_sessions: int = 1 << 30,
+                 stream=None, graphs: bool = False):
+        import torch
+        self.torch = torch
+        self.precision = precision
+        self.steps = int(steps_per_frame)
+        self.params = C.rdc_params_default(precision=precision, k_block=k_block)
+        if stream is None:
+            stream = torch.cuda.Stream()
+        self.stream = stream
+        self.batch = C.rdc_batch_create([], [self.params], stream=stream.cuda_stream)
+        C.rdc_batch_set_config(self.batch, max(1, k_block), 8, 64, graphs)
+        if memory_budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            memory_budget = int(free * 0.8)
+        self.budget = int(memory_budget)
+        self.used = 0
+        self.max_sessions = int(max_sessions)
+        self.waiting: collections.deque[Session] = collections.deque()
+        self.active: dict[int, Session] = {}
+        self.pending: dict[int, Frame] = {}      # sid -> requested frame not yet launched
+        self.inflight: list = []                 # (event, [frames])
+        self.completed: list[Frame] = []
+        self.ticks = 0
+        self.cells_stepped = 0.0
+        self.peak_sessions = 0
+
+    # -- sessions -------------------------------------------------------------
+    def arrive(self, s: Session, now: float | None = None):
+        s.arrival = time.perf_counter() if now is None else now
+        self.waiting.append(s)
+        self._admit()
+
+    def _admit(self):
+        while self.waiting and len(self.active) < self.max_sessions:
+            s = self.waiting[0]
+            need = s.state_bytes(self.precision)
+            if self.used + need > self.budget:
+                break
+            p = C.rdc_params_default(precision=self.precision, k_block=self.params.k_block)
+            if s.eps is not None:
+                p.eps = s.eps
+            s.slot = C.rdc_batch_add(self.batch, s.width, s.height, p, s.phi)
+            s.admitted_at = time.perf_counter()
+            self.used += need
+            self.waiting.popleft()
+            self.active[s.sid] = s
+            self.peak_sessions = max(self.peak_sessions, len(self.active))
+            self._request(s)
+
+    def _request(self, s: Session):
+        if s.done_frames < s.frames:
+            self.pending[s.sid] = Frame(s.sid, s.done_frames, time.perf_counter())
+
+    def _leave(self, s: Session):
+        C.rdc_batch_remove(self.batch, s.slot)
+        self.used -= s.state_bytes(self.precision)
+        del self.active[s.sid]
+        self._admit()
+
+    # -- the loop -------------------------------------------------------------
+    def tick(self) -> int:
+        """Launches one batched frame for every session with a pending
+        request and none in flight.  Returns the number of sessions stepped."""
+        busy = {f.sid for _, fs in self.inflight for f in fs}
+        ready = [sid for sid in self.pending if sid not in busy]
+        if not ready:
+            return 0
+        frames = []
+        slots = []
+        for sid in ready:
+            s = self.active[sid]
+            f = self.pending.pop(sid)
+            t = s.touches[f.index] if f.index < len(s.touches) else None
+            if t is not None:
+                C.rdc_batch_seed(self.batch, s.slot, *t)
+            slots.append(s.slot)
+            frames.append(f)
+            self.cells_stepped += s.width * s.height * self.steps
+        C.rdc_batch_step(self.batch, slots, self.steps)
+        ev = self.torch.cuda.Event()
+        ev.record(self.stream)
+        self.inflight.append((ev, frames))
+        self.ticks += 1
+        return len(ready)
+
+    def poll(self) -> int:
+        """Completes finished frames; returns how many completed."""
+        n = 0
+        still = []
+        for ev, frames in self.inflight:
+            if ev.query():
+                now = time.perf_counter()
+                for f in frames:
+                    f.completed = now
+                    self.completed.append(f)
+                    s = self.active[f.sid]
+                    s.done_frames += 1
+                    n += 1
+                    if s.done_frames >= s.frames:
+                        self._leave(s)
+                    else:
+                        self._request(s)
+            else:
+                still.append((ev, frames))
+        self.inflight = still
+        return n
+
+    def idle(self) -> bool:
+        return not (self.waiting or self.active or self.inflight)
+
+    def read(self, s: Session, dtype=np.float64):
+        u = np.empty((s.height, s.width), dtype=dtype)
+        v = np.empty_like(u)
+        C.rdc_batch_read(self.batch, s.slot, u, v)
+        return u, v
+
+    def close(self):
+        if self.batch:
+            C.rdc_batch_destroy(self.batch)
+            self.batch = None
+
+    def stats(self) -> dict:
+        lat = np.array([f.latency for f in self.completed]) * 1e3
+        return {"frames": len(self.completed),
+                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "max_ms": float(lat.max()) if len(lat) else None,
+                "ticks": self.ticks, "cells_stepped": self.cells_stepped,
+                "peak_sessions": self.peak_sessions}
+
+
+def run_workload(sessions, arrivals, server: Server, poll_sleep: float = 50e-6,
+                 on_complete=None, time_limit: float = 600.0):
+    """Drives a server through a list of sessions arriving at the given times
+    (seconds from start).  Returns (wall seconds, stats)."""
+    order = sorted(range(len(sessions)), key=lambda i: arrivals[i])
+    t0 = time.perf_counter()
+    nxt = 0
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < len(order) and arrivals[order[nxt]] <= now:
+            server.arrive(sessions[order[nxt]])
+            nxt += 1
+        server.poll()
+        launched = server.tick()
+        if nxt >= len(order) and server.idle():
+            break
+        if now > time_limit:
+            raise TimeoutError("serving workload did not finish")
+        if not launched:
+            time.sleep(poll_sleep)
+    server.torch.cuda.synchronize()
+    return time.perf_counter() - t0, server.stats()

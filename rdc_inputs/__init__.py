@@ -264,3 +264,44 @@ def sweep_batch(seed: int = 4, n_grids: int = 512, sizes=(128, 256, 512, 1024),
         disks.append([(float(a), float(b), float(c)) for a, b, c in zip(cx, cy, r)])
     return BatchSpec([int(n) for n in N], [float(p) for p in phi],
                      [float(e) for e in eps], disks)
+
+
+@dataclasses.dataclass
+class SessionSpec:
+    sid: int
+    size: int
+    phi: np.ndarray            # size x size float32
+    touches: list              # per frame: (cx, cy, r, value)
+    arrival: float             # seconds from the start
+
+
+def diode_sessions(seed: int = 5, n: int = 64, sizes=(512, 1024, 2048), rate: float = 20.0,
+                   frames: int = 20, touch_r: float = 6.0) -> list:
+    """Interactive sessions: Poisson arrivals at ``rate`` per second, square
+    grids of a random size, each a diode channel (see ``diode``) placed at a
+    random position and orientation in a phi = 0.2 background; each frame
+    starts with a u = 0.8 touch disk at a random point of the channel's anode
+    half."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for sid in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        N = int(rng.choice(np.asarray(sizes)))
+        band_h = 48
+        c = diode(N, band_h, flip=bool(rng.integers(0, 2)))
+        phi = np.full((N, N), PHI_PASSIVE_STRONG, dtype=np.float32)
+        y0 = int(rng.integers(0, N - band_h))
+        phi[y0:y0 + band_h, :] = c.phi.astype(np.float32)
+        ax, ay, _ = c.seeds["anode"]
+        vertical = bool(rng.integers(0, 2))
+        touches = []
+        lo, hi = (4.0, N / 2 - 10.0) if ax < N / 2 else (N / 2 + 10.0, N - 5.0)
+        for _ in range(frames):
+            x = float(rng.uniform(lo, hi))
+            y = float(y0 + ay + rng.uniform(-4, 4))
+            touches.append((y, x, touch_r, SEED_VALUE) if vertical else (x, y, touch_r, SEED_VALUE))
+        if vertical:
+            phi = np.ascontiguousarray(phi.T)
+        out.append(SessionSpec(sid, N, phi, touches, t))
+    return out

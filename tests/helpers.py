@@ -44,7 +44,7 @@ def gpu_run(pkg, W, H, phi=None, seeds=(), n=0, prec="f64", flags=0, k=1,
             cur = {f: getattr(s, f) for f, _ in s._fields_}
             cur.update(shape)
             pkg.rdc_set_shape(h, cur["bx"], cur["rows"], cur["tx"], cur["ty"],
-                              cur["nthreads"], cur["k"])
+                              cur["nthreads"], cur["k"], cur["variant"], cur["krows"])
         if state is not None:
             pkg.rdc_set_state(h, *state)
         for (cx, cy, r, val) in seeds:

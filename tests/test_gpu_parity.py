@@ -101,22 +101,26 @@ def test_f64_mixed_phi_bitwise(gpu, orc, om):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16", "f16"])
-@pytest.mark.parametrize("k", [2, 3, 4, 8])
-@pytest.mark.parametrize("W,H", [(130, 67), (257, 129), (1000, 37), (31, 300)])
-def test_kblock_bitwise(gpu, prec, k, W, H):
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 8])
+@pytest.mark.parametrize("W,H", [(130, 67), (257, 129), (1000, 37), (31, 300), (1, 9), (9, 1)])
+@pytest.mark.parametrize("variant", [0, 1], ids=["stream", "tile"])
+def test_kblock_bitwise(gpu, prec, k, W, H, variant):
     seeds = _centre_seed(W, H) + [(3.0, 5.0, 4.0, 0.8)]
     n = 4 * k + 3
     a, av, _ = gpu_run(gpu, W, H, seeds=seeds, n=n, prec=prec, k=1)
-    b, bv, ex = gpu_run(gpu, W, H, seeds=seeds, n=n, prec=prec, k=k)
+    b, bv, ex = gpu_run(gpu, W, H, seeds=seeds, n=n, prec=prec, k=k,
+                        shape=dict(variant=variant, krows=29))
     assert np.array_equal(a, b) and np.array_equal(av, bv)
     assert ex["view"].launches == n // k + n % k
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("shape", [dict(bx=32, rows=1), dict(bx=64, rows=3), dict(bx=256, rows=64),
-                                   dict(tx=16, ty=8, nthreads=64, k=4),
-                                   dict(tx=100, ty=20, nthreads=512, k=4),
-                                   dict(tx=7, ty=45, nthreads=96, k=2)])
+                                   dict(tx=16, ty=8, nthreads=64, k=4, variant=1),
+                                   dict(tx=100, ty=20, nthreads=512, k=4, variant=1),
+                                   dict(tx=7, ty=45, nthreads=96, k=2, variant=1),
+                                   dict(k=4, krows=1), dict(k=8, krows=7), dict(k=3, krows=1000),
+                                   dict(k=6, krows=40)])
 def test_shape_invariance(gpu, prec, shape):
     W, H = 301, 157
     seeds = _centre_seed(W, H)

@@ -1,0 +1,100 @@
+"""Continuous-batching serving loop: sessions arriving while others run are
+admitted as memory frees up, their frames share batched launches, and every
+session's final state equals the same session run alone, bit for bit."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import rdc_inputs as ri
+
+pytestmark = pytest.mark.gpu
+
+
+def _sessions(serve, n, seed=5, frames=6):
+    rng = np.random.default_rng(seed)
+    out = []
+    for sid in range(n):
+        N = int(rng.choice([64, 128, 192]))
+        c = ri.diode(N, N // 2 if N > 64 else 48)
+        H, W = c.phi.shape
+        touches = []
+        for f in range(frames):
+            if f % 2 == 0:
+                cx, cy, r = c.seeds["anode"]
+                touches.append((float(cx + rng.uniform(-2, 2)), float(cy), 4.0, 0.8))
+            else:
+                touches.append(None)
+        out.append(serve.Session(sid, W, H, phi=c.phi.astype(np.float32), frames=frames,
+                                 touches=touches))
+    return out
+
+
+def _alone(pkg, s, steps):
+    p = pkg.rdc_params_default(precision=0)
+    h = pkg.rdc_create(s.width, s.height, p, s.phi)
+    try:
+        for f in range(s.frames):
+            t = s.touches[f]
+            if t is not None:
+                pkg.rdc_seed(h, *t)
+            pkg.rdc_step(h, steps)
+        u = np.empty((s.height, s.width))
+        v = np.empty((s.height, s.width))
+        pkg.rdc_read(h, u, v)
+    finally:
+        pkg.rdc_destroy(h)
+    return u, v
+
+
+def test_serving_mix_equals_alone(gpu):
+    from paper_1901_06535_gb300 import serve
+    sessions = _sessions(serve, 10)
+    # a budget that fits only a few sessions at once: the rest wait to be admitted
+    budget = 3 * max(s.state_bytes(0) for s in sessions)
+    srv = serve.Server(precision=0, k_block=2, steps_per_frame=20, memory_budget=budget)
+    finals = {}
+    orig_leave = srv._leave
+
+    def leave(s):
+        finals[s.sid] = srv.read(s)
+        orig_leave(s)
+
+    srv._leave = leave
+    try:
+        arrivals = [0.002 * i for i in range(len(sessions))]
+        wall, st = serve.run_workload(sessions, arrivals, srv)
+    finally:
+        srv.close()
+    assert st["frames"] == sum(s.frames for s in sessions)
+    assert 1 <= st["peak_sessions"] <= 3
+    assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
+    for s in sessions:
+        u, v = finals[s.sid]
+        ua, va = _alone(gpu, s, 20)
+        assert np.array_equal(u, ua) and np.array_equal(v, va), s.sid
+
+
+def test_serving_overlapping_arrivals(gpu):
+    """All sessions at once, generous budget: many share each tick."""
+    from paper_1901_06535_gb300 import serve
+    sessions = _sessions(serve, 12, seed=9, frames=4)
+    srv = serve.Server(precision=0, k_block=4, steps_per_frame=16)
+    finals = {}
+    orig_leave = srv._leave
+
+    def leave(s):
+        finals[s.sid] = srv.read(s)
+        orig_leave(s)
+
+    srv._leave = leave
+    try:
+        wall, st = serve.run_workload(sessions, [0.0] * len(sessions), srv)
+    finally:
+        srv.close()
+    assert st["peak_sessions"] == len(sessions)
+    assert st["ticks"] < st["frames"]          # frames were batched together
+    for s in sessions[:4]:
+        u, _ = finals[s.sid]
+        ua, _ = _alone(gpu, s, 16)
+        assert np.array_equal(u, ua)

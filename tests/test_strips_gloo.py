@@ -1,0 +1,123 @@
+"""Multi-rank paths on CPU ranks (gloo, world size 2).
+
+1. Row-strip decomposition of one grid: each rank owns a strip of rows and
+   steps it with the FP64 oracle on the strip plus one halo row of u from each
+   neighbour, exchanged every step (v and phi are local: v does not diffuse,
+   Eq. 1, and phi is static).  The gathered result must equal the unsplit
+   oracle bit for bit -- the exchange a multi-GPU strip path would need.
+2. The benchmark's rank aggregation: the slowest rank's time and the
+   whole-job (weak-scaling) rate.
+"""
+from __future__ import annotations
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+W, H, STEPS = 37, 29, 120
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _initial():
+    import oracle
+    orc = oracle.load()
+    phi = np.full((H, W), 0.054)
+    phi[:, 20:23] = 0.0975
+    u, v = orc.rest_field(phi)
+    orc.seed_disk(u, 10.0, 14.0, 6.0, 0.8)
+    orc.seed_disk(u, 30.0, 3.0, 4.0, 1.0)
+    return orc, phi, u, v
+
+
+def _strip_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    orc, phi, u, v = _initial()
+    bounds = np.linspace(0, H, world + 1).astype(int)
+    r0, r1 = bounds[rank], bounds[rank + 1]
+    up = rank > 0            # a neighbour above
+    dn = rank < world - 1    # a neighbour below
+    us, vs, ph = u[r0:r1].copy(), v[r0:r1].copy(), phi[r0:r1]
+    for _ in range(STEPS):
+        halo_top = torch.empty(W, dtype=torch.float64)
+        halo_bot = torch.empty(W, dtype=torch.float64)
+        reqs = []
+        if up:
+            reqs.append(dist.isend(torch.from_numpy(us[0].copy()), rank - 1))
+            reqs.append(dist.irecv(halo_top, rank - 1))
+        if dn:
+            reqs.append(dist.isend(torch.from_numpy(us[-1].copy()), rank + 1))
+            reqs.append(dist.irecv(halo_bot, rank + 1))
+        for q in reqs:
+            q.wait()
+        rows_u = ([halo_top.numpy()] if up else []) + list(us) + ([halo_bot.numpy()] if dn else [])
+        ext_u = np.ascontiguousarray(np.stack(rows_u))
+        # v and phi of the halo rows only feed the halo rows' own (discarded) update
+        pad = lambda a: np.ascontiguousarray(np.concatenate(  # noqa: E731
+            ([a[:1]] if up else []) + [a] + ([a[-1:]] if dn else [])))
+        u1, v1, rc, _ = orc.step(pad(ph), ext_u, pad(vs))
+        a = 1 if up else 0
+        us = u1[a:a + (r1 - r0)].copy()
+        vs = v1[a:a + (r1 - r0)].copy()
+    if rank == 0:
+        parts_u, parts_v = [us], [vs]
+        for src in range(1, world):
+            n = (bounds[src + 1] - bounds[src]) * W
+            tu = torch.empty(n, dtype=torch.float64)
+            tv = torch.empty(n, dtype=torch.float64)
+            dist.recv(tu, src)
+            dist.recv(tv, src)
+            parts_u.append(tu.numpy().reshape(-1, W))
+            parts_v.append(tv.numpy().reshape(-1, W))
+        np.savez(out_path, u=np.concatenate(parts_u), v=np.concatenate(parts_v))
+    else:
+        dist.send(torch.from_numpy(us.ravel().copy()), 0)
+        dist.send(torch.from_numpy(vs.ravel().copy()), 0)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_row_strips_with_halo_exchange_equal_unsplit(tmp_path):
+    out = str(tmp_path / "strips.npz")
+    mp.start_processes(_strip_worker, args=(2, _free_port(), out), nprocs=2, join=True,
+                       start_method="spawn")
+    orc, phi, u, v = _initial()
+    ref = orc.run(phi, u, v, STEPS)
+    got = np.load(out)
+    assert np.array_equal(got["u"], ref["u"]) and np.array_equal(got["v"], ref["v"])
+
+
+def _agg_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t = [2.0, 3.0][rank]
+    t_max = bench.max_over_ranks(t, world)
+    val = bench.weak_scaling_value(1e9, world, t_max)
+    if rank == 0:
+        np.save(out_path, np.array([t_max, val]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_bench_rank_aggregation(tmp_path):
+    out = str(tmp_path / "agg.npy")
+    mp.start_processes(_agg_worker, args=(2, _free_port(), out), nprocs=2, join=True,
+                       start_method="spawn")
+    t_max, val = np.load(out)
+    assert t_max == 3.0
+    assert val == pytest.approx(2 * 1e9 / 3.0 / 1e9)
