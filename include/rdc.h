@@ -287,6 +287,48 @@ int rdc_get_shape(rdc_sim* sim, rdc_launch_shape* out);
 /* Replaces the launch shapes; RDC_EINVAL (and no change) if out of range. */
 int rdc_set_shape(rdc_sim* sim, const rdc_launch_shape* in);
 
+/*
+ * Allocation-free stepping (the paper has no counterpart; this is a
+ * deployment convenience).  Advances caller-owned device buffers by n >= 0
+ * Euler steps, exactly as rdc_step would (same kernels, same bits), and
+ * allocates no device memory: no cudaMalloc, no cudaFree, no allocating
+ * library call.  For callers that cannot allocate -- code running while a
+ * stream is being captured into a CUDA graph, hosts whose device memory comes
+ * from their own pool, loops where cudaMalloc's implicit device
+ * synchronisation is not acceptable.
+ *   g, p           : as rdc_create (p->k_block selects temporal blocking);
+ *   u_in, v_in     : current state, storage type of p->precision, never
+ *                    written;
+ *   phi            : phi map (float; double for RDC_F64) with the same pitch
+ *                    in elements as the state planes;
+ *   u_out, v_out   : receive the state after n steps (distinct from the
+ *                    inputs);
+ *   pitch_bytes    : row stride of the state planes, a multiple of 16 and of
+ *                    the element size, >= W * element size; all pointers
+ *                    16-byte aligned;
+ *   stream         : cudaStream_t, NULL = the legacy default stream;
+ *   first_bad      : NULL to skip the health check (the call is then fully
+ *                    asynchronous); otherwise the call runs the check of
+ *                    rdc_check on u_out, synchronises the stream, stores the
+ *                    first bad flat index (or -1) and returns
+ *                    RDC_ENONFINITE if one exists.
+ * Scratch: intermediate states of multi-step calls and the health flag live
+ * in one file-scope device array of 32 MiB that every GPU loading this
+ * library holds until the process exits.  A grid needs 256 + 2 *
+ * roundup256(pitch_bytes * H) bytes of it (FP32: about 4 M cells, e.g.
+ * 2048 x 2048); larger grids get RDC_EUNSUPPORTED before anything is
+ * enqueued.  The first call on each device looks the array's address up
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * previous call's contents (the flag is reset on every call): calls whose
+ * work overlaps on the GPU -- on different streams or different threads --
+ * race on it and must be serialised by the caller.
+ */
+int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_in,
+                     const void* v_in, const void* phi, void* u_out, void* v_out,
+                     size_t pitch_bytes, int64_t n, void* stream,
+                     int64_t* first_bad);
+
 /* ---- batches of independent grids ---------------------------------------- */
 /*
  * A batch holds many independent simulations (parameter sweeps, interactive

@@ -18,7 +18,7 @@ from ._capi import (  # noqa: F401  (re-exported C-ABI names)
     lib, rdc_check, rdc_create, rdc_create_ext, rdc_create_f64phi, rdc_destroy,
     rdc_get_shape, rdc_get_view, rdc_last_error, rdc_params, rdc_params_default,
     rdc_probe, rdc_read, rdc_reset_rest, rdc_rest_state, rdc_seed, rdc_set_phi,
-    rdc_set_shape, rdc_set_state, rdc_stability, rdc_status_str, rdc_step,
+    rdc_set_shape, rdc_set_state, rdc_stability, rdc_status_str, rdc_step, rdc_step_noalloc,
     rdc_sync, rdc_batch_add, rdc_batch_check, rdc_batch_create, rdc_batch_destroy,
     rdc_batch_get_info, rdc_batch_read, rdc_batch_remove, rdc_batch_seed, rdc_batch_set_config,
     rdc_batch_set_state, rdc_batch_step, rdc_batch_sync, rdc_batch_tune)

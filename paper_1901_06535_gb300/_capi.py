@@ -125,6 +125,9 @@ _SIGS = {
     "rdc_get_view": (ctypes.c_int, [_P, ctypes.POINTER(rdc_view)]),
     "rdc_get_shape": (ctypes.c_int, [_P, ctypes.POINTER(rdc_launch_shape)]),
     "rdc_set_shape": (ctypes.c_int, [_P, ctypes.POINTER(rdc_launch_shape)]),
+    "rdc_step_noalloc": (ctypes.c_int, [rdc_grid, ctypes.POINTER(rdc_params), _P, _P, _P, _P, _P,
+                                        ctypes.c_size_t, ctypes.c_int64, _P,
+                                        ctypes.POINTER(ctypes.c_int64)]),
     "rdc_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.POINTER(rdc_params), _P, _P,
                                         ctypes.POINTER(_P)]),
     "rdc_batch_add": (ctypes.c_int, [_P, rdc_grid, ctypes.POINTER(rdc_params), _P,
@@ -363,6 +366,22 @@ def rdc_get_view(h) -> rdc_view:
     v = rdc_view()
     _chk(lib().rdc_get_view(h, ctypes.byref(v)), "rdc_get_view")
     return v
+
+
+def rdc_step_noalloc(width: int, height: int, params: rdc_params, u_in: int, v_in: int,
+                     phi: int, u_out: int, v_out: int, pitch_bytes: int, n: int,
+                     stream=None, check: bool = True):
+    """Allocation-free stepping of caller-owned device buffers (pointers as
+    ints).  Returns (status, first_bad); with check=False the health check is
+    skipped and the call stays asynchronous."""
+    fb = ctypes.c_int64(-1)
+    s = _stream(stream)
+    rc = lib().rdc_step_noalloc(rdc_grid(int(width), int(height)), ctypes.byref(params),
+                                int(u_in), int(v_in), int(phi), int(u_out), int(v_out),
+                                int(pitch_bytes), int(n), None if s == CUDA_STREAM_LEGACY else s,
+                                ctypes.byref(fb) if check else None)
+    _chk(rc, "rdc_step_noalloc", allow=(RDC_ENONFINITE,))
+    return rc, fb.value
 
 
 def rdc_get_shape(h) -> rdc_launch_shape:
