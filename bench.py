@@ -41,6 +41,34 @@ BYTES_PER_CELL = {"f32": 20, "bf16": 12, "f16": 12, "f64": 40}
 METRIC = "GCUPS (cell-updates/s)"
 
 
+# Sources that define the single-step kernel; a traffic figure measured on
+# other sources is stale.
+KERNEL_SOURCES = ["paper_1901_06535_gb300/csrc/rdc_device.cuh",
+                  "paper_1901_06535_gb300/csrc/rdc_step_impl.cuh"]
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic(kernel: str, cells: int):
+    """DRAM bytes (read + write) per launch from the recorded ncu capture, or
+    None when there is none or the kernel changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("sources_sha256") != kernel_sources_sha256():
+        return None
+    return rec["bytes_per_cell"] * cells
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -288,13 +316,15 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         # temporal blocking and storage modes: effective GCUPS on the same grid
-        tb = {}
-        for k in (1, 2, 4, 8):
-            tb[str(k)] = _mode_gcups(pkg, stream, "f32", k, 1000)
+        tb = {"1": _mode_gcups(pkg, stream, "f32", 1, 1000)}
+        for k in (2, 3, 4, 6, 8):
+            tb[str(k)] = max(_mode_gcups(pkg, stream, "f32", k, 960, krows=kr) for kr in (64, 128))
+        tuned = _tuned(pkg, stream, "f32")
         modes = {m: _mode_gcups(pkg, stream, m, 1, 1000) for m in ("bf16", "f16")}
-        modes["bf16_k4"] = _mode_gcups(pkg, stream, "bf16", 4, 1000)
+        modes["bf16_tuned"] = _tuned(pkg, stream, "bf16")
+        modes["f16_tuned"] = _tuned(pkg, stream, "f16")
         modes["f64"] = _mode_gcups(pkg, stream, "f64", 1, 100)
-        extras = {"temporal_blocking_gcups": tb, "storage_modes_gcups": modes,
+        extras = {"temporal_blocking_gcups": tb, "tuned_f32": tuned, "storage_modes_gcups": modes,
                   "batch_sweep": _batch_sweep(pkg, stream), "serving": _serving(pkg)}
     e2e = None if args.no_extras else _e2e(pkg, stream, h, disks, nE, args)
 
@@ -319,7 +349,8 @@ def main():
                            "l2": "inputs larger than L2 (1.34 GB state), no flush"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak,
-                             "peak_kind": peak_kind, "traffic": None,
+                             "peak_kind": peak_kind,
+                             "traffic": _traffic("k_step1<float>", W * H) if args.kblock == 1 else None,
                              "kernel": "k_step1<float>" if args.kblock == 1 else "k_stepk_stream<float>",
                              "bytes_per_cell_update": BYTES_PER_CELL["f32"],
                              "launch_us": per_launch_s * 1e6},
@@ -334,12 +365,37 @@ def main():
     return 0
 
 
-def _mode_gcups(pkg, stream, mode, k, n):
+def _tuned(pkg, stream, mode, n=960):
+    """Autotuned shape on the 8192^2 grid and its GCUPS over n steps."""
+    import torch
+    prec = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}[mode]
+    h = pkg.rdc_create(W, H, pkg.rdc_params_default(precision=prec), None, stream.cuda_stream)
+    try:
+        pkg.rdc_seed(h, W / 2, H / 2, 10.0, 0.8)
+        shape, est = pkg.rdc_tune(h, 3)
+        pkg.rdc_step(h, 3 * shape["k"])
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        pkg.rdc_step(h, n)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return {"gcups": W * H * n / (a.elapsed_time(b) / 1e3) / 1e9, "k": shape["k"],
+                "variant": shape["variant"], "krows": shape["krows"], "rows": shape["rows"]}
+    finally:
+        pkg.rdc_destroy(h)
+
+
+def _mode_gcups(pkg, stream, mode, k, n, krows=None):
     import torch
     prec = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}[mode]
     p = pkg.rdc_params_default(precision=prec, k_block=k)
     h = pkg.rdc_create(W, H, p, None, stream.cuda_stream)
     try:
+        if krows is not None:
+            s = pkg.rdc_get_shape(h)
+            pkg.rdc_set_shape(h, s.bx, s.rows, s.tx, s.ty, s.nthreads, k, 0, krows)
         pkg.rdc_seed(h, W / 2, H / 2, 10.0, 0.8)
         pkg.rdc_step(h, 3 * k)
         a = torch.cuda.Event(enable_timing=True)
@@ -391,7 +447,7 @@ def _batch_sweep(pkg, stream, steps=5000):
         pkg.rdc_batch_destroy(b)
 
 
-def _serving(pkg, frames=20, steps_per_frame=50):
+def _serving(pkg, frames=100, steps_per_frame=50):
     """Interactive serving: 64 sessions arriving Poisson at 20/s (seed 5),
     grids U{512, 1024, 2048}^2 with diode maps at random positions and
     orientations, each requesting `frames` frames of `steps_per_frame` steps

@@ -99,7 +99,9 @@ typedef struct {
     int32_t precision; /* RDC_F32 / RDC_F64 / RDC_F32_BF16STORE / RDC_F32_F16STORE */
     int32_t flags;     /* RDC_DIFFUSION_ONLY | RDC_REACTION_ONLY (not both) */
     int32_t k_block;   /* Euler steps fused per launch (temporal blocking):
-                          0 = library default, 1 = one step per launch,
+                          0 = library default (4 for FP32-compute grids of
+                          >= 2^20 cells, else 1; see rdc_tune), 1 = one step
+                          per launch,
                           2..8 = k steps per launch.  Results are bitwise
                           identical for every k. */
     int32_t reserved;  /* must be 0 */
@@ -216,6 +218,74 @@ int rdc_check(rdc_sim* sim, int64_t* first_bad);
  * (as double).  Any index outside [0, W*H) gives RDC_EINVAL. */
 int rdc_probe(rdc_sim* sim, int32_t n, const int64_t* cells, double* out);
 
+/* ---- drawing substrate (§3) ---------------------------------------------- */
+/* Line width presets of §3, in cells (one pixel of the paper's simulation is
+ * one cell): permeable lines slow waves, semi-permeable lines pass waves that
+ * meet them head-on but not those running along them, impermeable lines stop
+ * all waves. */
+#define RDC_WIDTH_PERMEABLE 2
+#define RDC_WIDTH_SEMIPERMEABLE 3
+#define RDC_WIDTH_IMPERMEABLE 8
+#define RDC_SNAP_DEGREES 15.0  /* the "snap line" angle step of §3 */
+
+/*
+ * Rotates the segment (x0,y0)-(x1,y1) about (x0,y0) to the nearest multiple of
+ * snap_deg degrees, keeping its length, by exactly this FP64 sequence
+ * (no contraction; C math library cos/sin/atan2/hypot/round):
+ *   dx = x1 - x0; dy = y1 - y0; len = hypot(dx, dy);
+ *   a = atan2(dy, dx) * (180 / pi); a = round(a / snap_deg) * snap_deg;
+ *   r = a * (pi / 180); x1' = x0 + len cos(r); y1' = y0 + len sin(r).
+ * Host only; no GPU needed.
+ */
+int rdc_snap_segment(double x0, double y0, double x1, double y1, double snap_deg,
+                     double* x1_out, double* y1_out);
+
+/*
+ * Async.  Draws a straight line of substrate (§3): phi := value for every cell
+ * whose centre (j, i) lies within width/2 of the segment (x0,y0)-(x1,y1)
+ * (x along columns), the distance taken in FP64 without contraction:
+ *   t = clamp(((j - x0) ex + (i - y0) ey) / (ex^2 + ey^2), 0, 1),
+ *   (px, py) = (x0 + t ex, y0 + t ey), in if (j - px)^2 + (i - py)^2 <= (width/2)^2.
+ * snap_deg > 0 first snaps the segment with rdc_snap_segment.  u and v are
+ * unchanged; value must admit a rest state (as for phi maps).
+ */
+int rdc_draw_line(rdc_sim* sim, double x0, double y0, double x1, double y1, double width,
+                  double value, double snap_deg);
+
+/* Async.  phi := value everywhere (the filled / empty background presets of
+ * §3); u and v are unchanged. */
+int rdc_fill_phi(rdc_sim* sim, double value);
+
+/* Synchronous.  Copies the phi map into a packed H*W host array of dtype
+ * RDC_DTYPE_F32 or RDC_DTYPE_F64 (for saving circuits and backgrounds). */
+int rdc_read_phi(rdc_sim* sim, void* out, int32_t dtype);
+
+/* ---- outputs (§3.1) ------------------------------------------------------- */
+#define RDC_RENDER_SNAPSHOT 0   /* the current state */
+#define RDC_RENDER_TIMELAPSE 1  /* the timelapse record over the substrate */
+
+/*
+ * Renders a W*H RGBA8 image (row-major, 4 bytes per pixel, alpha 255) with the
+ * paper's colour mapping (§3.1): red = u, green = inhibitive substrate, blue
+ * = v.  Per cell, in FP32: R = rint(255 * clamp(u * u_scale, 0, 1)) (round
+ * half to even), B likewise from v and v_scale, G = 255 where phi >=
+ * phi_threshold (compared in FP64) else 0.  RDC_RENDER_TIMELAPSE takes R from
+ * the timelapse record instead of u and sets B = 0.
+ *   rgba          : host buffer (out_on_device = 0; the call synchronises) or
+ *                   device buffer (out_on_device = 1, 4-byte aligned; async).
+ * RDC_EINVAL for a timelapse render before any rdc_timelapse_record.
+ */
+int rdc_render(rdc_sim* sim, int32_t what, float u_scale, float v_scale,
+               double phi_threshold, void* rgba, int32_t out_on_device);
+
+/*
+ * Async.  Timelapse (§3.1: u recorded over time, overlaid on the static
+ * substrate): keeps, per cell, the running maximum of u (as FP32) over the
+ * states at which this is called; reset = 1 (or the first call) restarts it
+ * from the current u.  The record is allocated on first use.
+ */
+int rdc_timelapse_record(rdc_sim* sim, int32_t reset);
+
 /* Waits until all work enqueued on the simulation's stream is done. */
 int rdc_sync(rdc_sim* sim);
 
@@ -280,6 +350,17 @@ typedef struct {
                           test modes fall back to 1), 1 = shared-memory tile */
     int32_t krows;     /* register-streamed kernel: rows marched per CTA, >= 1 */
 } rdc_launch_shape;
+
+/*
+ * Autotuner: times reps launches of each candidate shape (single step with
+ * 4..32 rows per CTA; k in {2, 3, 4, 6, 8} with the register-streamed kernel
+ * at 32..256 rows per CTA -- full model only -- and with the shared-memory
+ * tile kernel), keeps the fastest in cell-updates per second and reports it
+ * in *out and *best_gcups (both optional).  Every timed launch reads the
+ * current state and writes the spare buffers, so tuning neither advances nor
+ * changes the state, and any pick gives the same bits.
+ */
+int rdc_tune(rdc_sim* sim, int32_t reps, rdc_launch_shape* out, double* best_gcups);
 
 /* Current launch shapes (set at create from the grid size and k_block). */
 int rdc_get_shape(rdc_sim* sim, rdc_launch_shape* out);

@@ -15,6 +15,10 @@ Parity status of the functions (what pins each one is in ``tests/``):
                                 analytic Jacobian, symmetries, 1-D reduction,
                                 AND-gate and diode behaviour of §4)
   * seed_disk                -- pinned (Gauss circle counts)
+  * draw_line / snap_segment -- pinned (line widths of the §3 presets, snapped
+                                angles and preserved length)
+  * render / timelapse       -- pinned (channel assignment of §3.1, clamping,
+                                round-half-even codes, running maximum)
   * arrival times in run     -- parity unpinned: the paper prints no wave
                                 speeds or arrival times; only the
                                 interpolation rule itself is checked.
@@ -133,6 +137,17 @@ class Oracle:
                                 ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                 i64p, ctypes.c_double, dp, i64p, i64p]
         lib.orc_run.restype = ctypes.c_int
+        fp = ctypes.POINTER(ctypes.c_float)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.orc_render.argtypes = [ctypes.c_int64, fp, fp, dp, fp, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_double, u8p]
+        lib.orc_render.restype = None
+        lib.orc_timelapse.argtypes = [ctypes.c_int64, fp, fp, ctypes.c_int32]
+        lib.orc_timelapse.restype = None
+        lib.orc_snap_segment.argtypes = [ctypes.c_double] * 5 + [dp, dp]
+        lib.orc_snap_segment.restype = ctypes.c_int
+        lib.orc_draw_line.argtypes = [ctypes.c_int32, ctypes.c_int32, dp] + [ctypes.c_double] * 6
+        lib.orc_draw_line.restype = ctypes.c_int64
         lib.orc_max_threads.argtypes = []
         lib.orc_max_threads.restype = ctypes.c_int32
         self.lib = lib
@@ -213,6 +228,50 @@ class Oracle:
             raise MemoryError("orc_run: out of memory")
         return {"u": u, "v": v, "status": rc, "bad_step": bs.value,
                 "bad_index": bi.value, "t_arr": t_arr[:len(pr)]}
+
+    # -- drawing (§3) -----------------------------------------------------------
+    def snap_segment(self, x0, y0, x1, y1, snap=15.0):
+        a = ctypes.c_double()
+        b = ctypes.c_double()
+        rc = self.lib.orc_snap_segment(x0, y0, x1, y1, snap, ctypes.byref(a), ctypes.byref(b))
+        if rc != OK:
+            raise ValueError("snap_segment: invalid arguments")
+        return a.value, b.value
+
+    def draw_line(self, phi, x0, y0, x1, y1, width, value, snap=0.0):
+        """In place on a float64 H x W map; returns the number of cells set."""
+        assert phi.dtype == np.float64 and phi.flags.c_contiguous
+        if snap > 0:
+            x1, y1 = self.snap_segment(x0, y0, x1, y1, snap)
+        H, W = phi.shape
+        return int(self.lib.orc_draw_line(W, H, _dptr(phi), x0, y0, x1, y1, width, value))
+
+    # -- outputs (§3.1) --------------------------------------------------------
+    def render(self, u, v, phi, u_scale=1.0, v_scale=1.0, thr=0.07575, tl=None):
+        """RGBA8 image (H, W, 4) of float32 u, v (or of the timelapse tl)."""
+        fp = ctypes.POINTER(ctypes.c_float)
+        u = np.ascontiguousarray(u, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        H, W = u.shape
+        out = np.empty((H, W, 4), dtype=np.uint8)
+        tlp = None
+        if tl is not None:
+            tl = np.ascontiguousarray(tl, dtype=np.float32)
+            tlp = tl.ctypes.data_as(fp)
+        self.lib.orc_render(u.size, u.ctypes.data_as(fp), v.ctypes.data_as(fp), _dptr(phi), tlp,
+                            float(u_scale), float(v_scale), float(thr),
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+        return out
+
+    def timelapse(self, u, tl=None):
+        """Returns the record updated with float32 u (a new record if tl is None)."""
+        fp = ctypes.POINTER(ctypes.c_float)
+        u = np.ascontiguousarray(u, dtype=np.float32)
+        reset = tl is None
+        tl = np.empty_like(u) if reset else np.array(tl, dtype=np.float32, copy=True)
+        self.lib.orc_timelapse(u.size, u.ctypes.data_as(fp), tl.ctypes.data_as(fp), int(reset))
+        return tl
 
     def max_threads(self) -> int:
         return int(self.lib.orc_max_threads())

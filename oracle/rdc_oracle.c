@@ -326,3 +326,99 @@ int32_t orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------- */
+/* Outputs (§3.1): red = u, green = inhibitive substrate, blue = v           */
+/* ------------------------------------------------------------------------- */
+
+/* 255 * clamp(x * scale, 0, 1), rounded half to even; every step in FP32
+ * (the paper fixes no precision for the picture; the CUDA path renders in
+ * FP32, and an 8-bit code must be decided in one precision on both sides). */
+static unsigned char orc_chan(float x, float scale)
+{
+    float y = x * scale;
+    if (y < 0.0f) y = 0.0f;
+    if (y > 1.0f) y = 1.0f;
+    return (unsigned char)lrintf(255.0f * y);
+}
+
+/* RGBA8 image (row-major, 4 bytes per cell).  tl == NULL: R from u, B from
+ * v; otherwise R from the timelapse record tl and B = 0.  G = 255 where
+ * phi >= thr (in FP64), else 0.  A = 255. */
+void orc_render(int64_t n, const float* u, const float* v, const double* phi,
+                const float* tl, float u_scale, float v_scale, double thr,
+                unsigned char* out)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        unsigned char r, b;
+        if (tl) {
+            r = orc_chan(tl[k], u_scale);
+            b = 0;
+        } else {
+            r = orc_chan(u[k], u_scale);
+            b = orc_chan(v[k], v_scale);
+        }
+        out[4 * k + 0] = r;
+        out[4 * k + 1] = (phi[k] >= thr) ? 255 : 0;
+        out[4 * k + 2] = b;
+        out[4 * k + 3] = 255;
+    }
+}
+
+/* Timelapse record: tl := u (reset) or max(tl, u), per cell, in FP32. */
+void orc_timelapse(int64_t n, const float* u, float* tl, int32_t reset)
+{
+    for (int64_t k = 0; k < n; ++k)
+        tl[k] = (reset || u[k] > tl[k]) ? u[k] : tl[k];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Drawing substrate (§3): lines of a given width, optional angle snapping   */
+/* ------------------------------------------------------------------------- */
+
+/* Rotates (x0,y0)-(x1,y1) about (x0,y0) to the nearest multiple of snap
+ * degrees, keeping its length (the app's "snap line", 15 degrees). */
+int orc_snap_segment(double x0, double y0, double x1, double y1, double snap,
+                     double* x1o, double* y1o)
+{
+    if (!x1o || !y1o || !(snap > 0.0)) return ORC_EINVAL;
+    const double dx = x1 - x0, dy = y1 - y0;
+    const double len = hypot(dx, dy);
+    double a = atan2(dy, dx) * (180.0 / 3.14159265358979323846);
+    a = round(a / snap) * snap;
+    const double r = a * (3.14159265358979323846 / 180.0);
+    *x1o = x0 + len * cos(r);
+    *y1o = y0 + len * sin(r);
+    return ORC_OK;
+}
+
+/* phi := value for every cell whose centre (x = j, y = i) lies within
+ * width/2 of the segment: the nearest point of the segment is x0 + t e with
+ * t the clamped projection of the cell onto e = (x1 - x0, y1 - y0).
+ * Returns the number of cells set. */
+int64_t orc_draw_line(int32_t W, int32_t H, double* phi, double x0, double y0,
+                      double x1, double y1, double width, double value)
+{
+    if (W < 1 || H < 1 || !phi || !(width >= 0.0)) return -1;
+    const double ex = x1 - x0, ey = y1 - y0;
+    const double L2 = ex * ex + ey * ey;
+    const double h = 0.5 * width;
+    const double half2 = h * h;
+    int64_t count = 0;
+    for (int32_t i = 0; i < H; ++i) {
+        for (int32_t j = 0; j < W; ++j) {
+            const double x = (double)j, y = (double)i;
+            double t = 0.0;
+            if (L2 > 0.0) t = ((x - x0) * ex + (y - y0) * ey) / L2;
+            if (t < 0.0) t = 0.0;
+            if (t > 1.0) t = 1.0;
+            const double px = x0 + t * ex, py = y0 + t * ey;
+            const double dx = x - px, dy = y - py;
+            if (dx * dx + dy * dy <= half2) {
+                phi[(int64_t)i * W + j] = value;
+                ++count;
+            }
+        }
+    }
+    return count;
+}

@@ -145,6 +145,16 @@ _SIGS = {
                                             ctypes.c_int32]),
     "rdc_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(rdc_batch_info)]),
     "rdc_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_batch_info)]),
+    "rdc_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_launch_shape),
+                                ctypes.POINTER(ctypes.c_double)]),
+    "rdc_snap_segment": (ctypes.c_int, [ctypes.c_double] * 5 +
+                         [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "rdc_draw_line": (ctypes.c_int, [_P] + [ctypes.c_double] * 7),
+    "rdc_fill_phi": (ctypes.c_int, [_P, ctypes.c_double]),
+    "rdc_read_phi": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "rdc_render": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_double, _P, ctypes.c_int32]),
+    "rdc_timelapse_record": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rdc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "rdc_last_error": (ctypes.c_char_p, []),
 }
@@ -382,6 +392,67 @@ def rdc_step_noalloc(width: int, height: int, params: rdc_params, u_in: int, v_i
                                 ctypes.byref(fb) if check else None)
     _chk(rc, "rdc_step_noalloc", allow=(RDC_ENONFINITE,))
     return rc, fb.value
+
+
+RDC_WIDTH_PERMEABLE = 2
+RDC_WIDTH_SEMIPERMEABLE = 3
+RDC_WIDTH_IMPERMEABLE = 8
+RDC_SNAP_DEGREES = 15.0
+
+
+def rdc_snap_segment(x0, y0, x1, y1, snap_deg=RDC_SNAP_DEGREES):
+    a = ctypes.c_double()
+    b = ctypes.c_double()
+    _chk(lib().rdc_snap_segment(float(x0), float(y0), float(x1), float(y1), float(snap_deg),
+                                ctypes.byref(a), ctypes.byref(b)), "rdc_snap_segment")
+    return a.value, b.value
+
+
+def rdc_draw_line(h, x0, y0, x1, y1, width, value, snap_deg=0.0) -> int:
+    return _chk(lib().rdc_draw_line(h, float(x0), float(y0), float(x1), float(y1), float(width),
+                                    float(value), float(snap_deg)), "rdc_draw_line")
+
+
+def rdc_read_phi(h, dtype=np.float64) -> np.ndarray:
+    view = rdc_get_view(h)
+    out = np.empty((view.height, view.width), dtype=dtype)
+    ptr, code, _ = _host_ptr(out, "out")
+    _chk(lib().rdc_read_phi(h, ptr, code), "rdc_read_phi")
+    return out
+
+
+def rdc_fill_phi(h, value) -> int:
+    return _chk(lib().rdc_fill_phi(h, float(value)), "rdc_fill_phi")
+
+
+RDC_RENDER_SNAPSHOT = 0
+RDC_RENDER_TIMELAPSE = 1
+
+
+def rdc_render(h, what: int = RDC_RENDER_SNAPSHOT, u_scale: float = 1.0, v_scale: float = 1.0,
+               phi_threshold: float = 0.07575, out=None):
+    """RGBA8 image as an (H, W, 4) uint8 array (a new host array unless `out`
+    -- a host array or a CUDA tensor -- is given)."""
+    view = rdc_get_view(h)
+    if out is None:
+        out = np.empty((view.height, view.width, 4), dtype=np.uint8)
+    on_dev = 1 if (hasattr(out, "is_cuda") and out.is_cuda) else 0
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    _chk(lib().rdc_render(h, int(what), float(u_scale), float(v_scale), float(phi_threshold),
+                          ptr, on_dev), "rdc_render")
+    return out
+
+
+def rdc_timelapse_record(h, reset: bool = False) -> int:
+    return _chk(lib().rdc_timelapse_record(h, int(bool(reset))), "rdc_timelapse_record")
+
+
+def rdc_tune(h, reps: int = 3):
+    """(shape dict, best GCUPS measured)."""
+    sh = rdc_launch_shape()
+    g = ctypes.c_double()
+    _chk(lib().rdc_tune(h, int(reps), ctypes.byref(sh), ctypes.byref(g)), "rdc_tune")
+    return {f: getattr(sh, f) for f, _ in sh._fields_}, g.value
 
 
 def rdc_get_shape(h) -> rdc_launch_shape:

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "rdc.h"
 #include "rdc_host.h"
@@ -166,6 +167,8 @@ struct rdc_sim {
     bool owns_misc = false;
     void* stage = nullptr;
     size_t stage_bytes = 0;
+    float* timelapse = nullptr;   // running maximum of u (lazily allocated)
+    bool timelapse_set = false;
     int64_t steps_done = 0, launches = 0;
     double phi_max = 0.0;
     Shape1 shape1{128, 16};
@@ -254,13 +257,21 @@ static void default_shapes(rdc_sim* s)
         s->shapek = ShapeK{32, 32, 1, 256};
     else
         s->shapek = ShapeK{64, 32, 1, 256};
-    s->shapek.k = s->p.k_block == 0 ? 1 : s->p.k_block;
+    // k_block = 0: temporal blocking (4 steps per launch) for grids of a
+    // million cells or more in the FP32-compute modes, where HBM would
+    // otherwise bound a single step; FP64 is bound by its arithmetic, so one
+    // step per launch.  rdc_tune measures instead of guessing.
+    int kdef = 1;
+    if (s->p.k_block == 0 && s->prec != P_F64 && s->mode == MODE_FULL &&
+        (int64_t)s->W * s->H >= (1 << 20))
+        kdef = 4;
+    s->shapek.k = s->p.k_block == 0 ? kdef : s->p.k_block;
     s->shapek.variant = 0;
     // rows per CTA of the streamed kernel: long enough that the 2k rows of
-    // overlap cost little, short enough for ~2.5 waves of warps (~24
-    // resident per SM)
-    int krows = 256;
-    while (krows > 32 && (int64_t)((s->W + 111) / 112) * ((s->H + krows - 1) / krows) < 152 * 48)
+    // overlap cost little (measured best: 64 for k <= 4, 128 beyond, on large
+    // grids), shorter on small grids so that every SM gets warps
+    int krows = s->shapek.k >= 5 ? 128 : 64;
+    while (krows > 16 && (int64_t)((s->W + 111) / 112) * ((s->H + krows - 1) / krows) < 152 * 16)
         krows /= 2;
     s->shapek.krows = krows;
 }
@@ -272,6 +283,7 @@ static void destroy_impl(rdc_sim* s)
     if (s->owns && s->base) cudaFree(s->base);
     if (s->owns_misc && s->misc) cudaFree(s->misc);
     if (s->stage) cudaFree(s->stage);
+    if (s->timelapse) cudaFree(s->timelapse);
     if (s->owns_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -623,6 +635,118 @@ int rdc_probe(rdc_sim* s, int32_t n, const int64_t* cells, double* out)
     return RDC_OK;
 }
 
+int rdc_snap_segment(double x0, double y0, double x1, double y1, double snap_deg,
+                     double* x1s, double* y1s)
+{
+    if (!x1s || !y1s || !std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(x1) ||
+        !std::isfinite(y1) || !(snap_deg > 0.0) || !std::isfinite(snap_deg))
+        return RDC_EINVAL;
+    // The documented sequence; host code is compiled without contraction.
+    const double dx = x1 - x0, dy = y1 - y0;
+    const double len = std::hypot(dx, dy);
+    double a = std::atan2(dy, dx) * (180.0 / 3.14159265358979323846);
+    a = std::round(a / snap_deg) * snap_deg;
+    const double r = a * (3.14159265358979323846 / 180.0);
+    *x1s = x0 + len * std::cos(r);
+    *y1s = y0 + len * std::sin(r);
+    return RDC_OK;
+}
+
+int rdc_draw_line(rdc_sim* s, double x0, double y0, double x1, double y1, double width,
+                  double value, double snap_deg)
+{
+    if (!s || !std::isfinite(x0) || !std::isfinite(y0) || !std::isfinite(x1) ||
+        !std::isfinite(y1) || !(width >= 0.0) || !(width < 1e7) || !host_phi_ok(value, &s->p) ||
+        !(snap_deg >= 0.0) || !std::isfinite(snap_deg))
+        return RDC_EINVAL;
+    if (snap_deg > 0.0) {
+        int rc = rdc_snap_segment(x0, y0, x1, y1, snap_deg, &x1, &y1);
+        if (rc) return rc;
+    }
+    CK(launch_draw_line(s->prec, s->phi, s->W, s->H, s->pitch, x0, y0, x1, y1, width, value,
+                        s->stream),
+       "draw kernel");
+    if (value > s->phi_max) s->phi_max = value;
+    return RDC_OK;
+}
+
+int rdc_read_phi(rdc_sim* s, void* out, int32_t dtype)
+{
+    if (!s || !out || (dtype != RDC_DTYPE_F32 && dtype != RDC_DTYPE_F64)) return RDC_EINVAL;
+    const int pb = phi_bytes(s->prec);
+    const bool direct = (dtype == RDC_DTYPE_F32 && pb == 4) || (dtype == RDC_DTYPE_F64 && pb == 8);
+    if (direct) {
+        CK(cudaMemcpy2DAsync(out, (size_t)s->W * pb, s->phi, (size_t)s->pitch * pb,
+                             (size_t)s->W * pb, s->H, cudaMemcpyDeviceToHost, s->stream),
+           "cudaMemcpy2DAsync(phi)");
+    } else {
+        const size_t bytes = (size_t)s->W * s->H * dtype_bytes(dtype);
+        int rc = ensure_stage(s, bytes);
+        if (rc) return rc;
+        // phi planes are float or double: the state conversion kernels apply
+        CK(launch_pack_out(pb == 8 ? P_F64 : P_F32, dtype, s->phi, s->stage, s->W, s->H,
+                           s->pitch, s->stream),
+           "phi conversion kernel");
+        CK(cudaMemcpyAsync(out, s->stage, bytes, cudaMemcpyDeviceToHost, s->stream),
+           "cudaMemcpyAsync(phi)");
+    }
+    CK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    return RDC_OK;
+}
+
+int rdc_fill_phi(rdc_sim* s, double value)
+{
+    if (!s || !host_phi_ok(value, &s->p)) return RDC_EINVAL;
+    CK(launch_fill_phi(s->prec, s->phi, s->W, s->H, s->pitch, value, s->stream), "fill kernel");
+    s->phi_max = value;
+    return RDC_OK;
+}
+
+int rdc_timelapse_record(rdc_sim* s, int32_t reset)
+{
+    if (!s || reset < 0 || reset > 1) return RDC_EINVAL;
+    if (!s->timelapse) {
+        CK(cudaMalloc((void**)&s->timelapse, (size_t)s->pitch * s->H * sizeof(float)),
+           "cudaMalloc(timelapse)");
+        reset = 1;
+    }
+    if (!s->timelapse_set) reset = 1;
+    CK(launch_timelapse(s->prec, s->u[s->cur], s->timelapse, s->W, s->H, s->pitch, s->pitch,
+                        reset, s->stream),
+       "timelapse kernel");
+    s->timelapse_set = true;
+    return RDC_OK;
+}
+
+int rdc_render(rdc_sim* s, int32_t what, float u_scale, float v_scale, double phi_threshold,
+               void* rgba, int32_t out_on_device)
+{
+    if (!s || !rgba || (what != 0 && what != 1) || !std::isfinite(u_scale) ||
+        !std::isfinite(v_scale) || std::isnan(phi_threshold) ||
+        (out_on_device != 0 && out_on_device != 1))
+        return RDC_EINVAL;
+    if (what == 1 && !s->timelapse_set) return RDC_EINVAL;
+    const size_t bytes = (size_t)s->W * s->H * 4;
+    void* dst = rgba;
+    if (!out_on_device) {
+        int rc = ensure_stage(s, bytes);
+        if (rc) return rc;
+        dst = s->stage;
+    } else if ((uintptr_t)rgba % 4) {
+        return RDC_EINVAL;
+    }
+    CK(launch_render(s->prec, s->u[s->cur], s->v[s->cur], s->phi,
+                     what == 1 ? s->timelapse : nullptr, s->W, s->H, s->pitch, s->pitch, u_scale,
+                     v_scale, phi_threshold, dst, s->stream),
+       "render kernel");
+    if (!out_on_device) {
+        CK(cudaMemcpyAsync(rgba, dst, bytes, cudaMemcpyDeviceToHost, s->stream),
+           "cudaMemcpyAsync(render)");
+        CK(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    }
+    return RDC_OK;
+}
+
 int rdc_sync(rdc_sim* s)
 {
     if (!s) return RDC_EINVAL;
@@ -724,6 +848,72 @@ int rdc_set_shape(rdc_sim* s, const rdc_launch_shape* in)
     s->shape1 = Shape1{in->bx, in->rows};
     s->shapek = sk;
     return RDC_OK;
+}
+
+int rdc_tune(rdc_sim* s, int32_t reps, rdc_launch_shape* out, double* best_gcups)
+{
+    if (!s || reps < 1) return RDC_EINVAL;
+    const ModelD m = model_of(s->p);
+    const Planes g{s->u[s->cur], s->v[s->cur], s->phi, s->u[1 - s->cur], s->v[1 - s->cur],
+                   s->W, s->H, s->pitch};
+    const double cells = (double)s->W * s->H;
+    struct Cand {
+        bool kblock;  // false: single-step kernel with s1; true: k-step kernel with sk
+        Shape1 s1;
+        ShapeK sk;
+    };
+    std::vector<Cand> cands;
+    ShapeK k1 = s->shapek;
+    k1.k = 1;
+    for (int rows : {4, 8, 16, 32}) cands.push_back({false, Shape1{s->shape1.bx, rows}, k1});
+    for (int k : {2, 3, 4, 6, 8}) {
+        if (s->mode == MODE_FULL)  // the streamed kernel serves the full model only
+            for (int krows : {32, 64, 128, 256})
+                cands.push_back({true, s->shape1, ShapeK{64, 32, k, 256, 0, krows}});
+        for (int ty : {32, 64})
+            cands.push_back({true, s->shape1, ShapeK{64, ty, k, ty == 64 ? 512 : 256, 1, 64}});
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "cudaEventCreate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return RDC_ECUDA;
+    }
+    double best = -1.0;
+    Cand pick{s->shapek.k > 1, s->shape1, s->shapek};
+    int rc = RDC_OK;
+    for (const Cand& c : cands) {
+        const bool use_k = c.kblock;
+        if (use_k && c.sk.variant == 1 && stepk_smem_bytes(s->prec, c.sk) > 227 * 1024) continue;
+        // each timed launch reads the current buffers and writes the spare ones
+        auto launch = [&]() {
+            return use_k ? launch_kblock(s->prec, s->mode, g, m, c.sk, s->stream)
+                         : launch_step1(s->prec, s->mode, g, m, c.s1, s->stream);
+        };
+        cudaError_t e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = host_cuda_fail(e, "autotune launch");
+            break;
+        }
+        const double rate = cells * (use_k ? c.sk.k : 1) * reps / (ms * 1e-3);
+        if (rate > best) {
+            best = rate;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    s->shape1 = pick.s1;
+    s->shapek = pick.sk;
+    if (best_gcups) *best_gcups = best / 1e9;
+    return out ? rdc_get_shape(s, out) : RDC_OK;
 }
 
 const char* rdc_status_str(int status)

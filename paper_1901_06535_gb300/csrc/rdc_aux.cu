@@ -157,6 +157,86 @@ __global__ void k_probe(const S* __restrict__ u, int W, int64_t pitch,
 }
 
 // ---------------------------------------------------------------------------
+// drawing substrate (§3): phi := value within width/2 of a segment
+// ---------------------------------------------------------------------------
+
+template <typename P>
+__global__ void k_draw_line(P* __restrict__ phi, int W, int H, int64_t pitch, int i0, int j0,
+                            int ni, int nj, double x0, double y0, double x1, double y1,
+                            double half2, P value)
+{
+    const double ex = __dsub_rn(x1, x0), ey = __dsub_rn(y1, y0);
+    const double L2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+    const int64_t n = (int64_t)ni * nj;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = i0 + (int)(k / nj);
+        const int j = j0 + (int)(k % nj);
+        const double x = (double)j, y = (double)i;
+        double t = 0.0;
+        if (L2 > 0.0)
+            t = __ddiv_rn(__dadd_rn(__dmul_rn(__dsub_rn(x, x0), ex), __dmul_rn(__dsub_rn(y, y0), ey)),
+                          L2);
+        t = fmin(fmax(t, 0.0), 1.0);
+        const double px = __dadd_rn(x0, __dmul_rn(t, ex));
+        const double py = __dadd_rn(y0, __dmul_rn(t, ey));
+        const double dx = __dsub_rn(x, px), dy = __dsub_rn(y, py);
+        if (__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= half2)
+            phi[(int64_t)i * pitch + j] = value;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// rendering (§3.1): red = u, green = inhibitive substrate, blue = v
+// ---------------------------------------------------------------------------
+
+// 255 * clamp(x * scale, 0, 1) rounded half to even, all in FP32.
+__device__ __forceinline__ unsigned int chan(float x, float scale)
+{
+    const float y = fminf(fmaxf(__fmul_rn(x, scale), 0.0f), 1.0f);
+    return (unsigned int)__float2int_rn(__fmul_rn(255.0f, y));
+}
+
+template <typename S>
+__global__ void k_render(const S* __restrict__ u, const S* __restrict__ v,
+                         const typename Traits<S>::PhiT* __restrict__ phi,
+                         const float* __restrict__ tl, int W, int H, int64_t pitch,
+                         int64_t tl_pitch, float u_scale, float v_scale, double thr,
+                         uchar4* __restrict__ out)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        const int64_t o = i * pitch + j;
+        unsigned int r, b;
+        if (tl) {  // timelapse: running maximum of u over the static substrate
+            r = chan(tl[i * tl_pitch + j], u_scale);
+            b = 0;
+        } else {
+            r = chan((float)widen(u[o]), u_scale);
+            b = chan((float)widen(v[o]), v_scale);
+        }
+        const unsigned int g = ((double)phi[o] >= thr) ? 255u : 0u;
+        out[k] = make_uchar4((unsigned char)r, (unsigned char)g, (unsigned char)b, 255);
+    }
+}
+
+template <typename S>
+__global__ void k_timelapse(const S* __restrict__ u, float* __restrict__ tl, int W, int H,
+                            int64_t pitch, int64_t tl_pitch, int reset)
+{
+    const int64_t n = (int64_t)W * H;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        const float x = (float)widen(u[i * pitch + j]);
+        float* t = tl + i * tl_pitch + j;
+        *t = reset ? x : fmaxf(*t, x);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 
@@ -324,6 +404,62 @@ cudaError_t launch_fill_phi(int prec, void* dst, int W, int H, int64_t pitch,
         k_fill<double><<<b, t, 0, st>>>((double*)dst, W, H, pitch, value);
     else
         k_fill<float><<<b, t, 0, st>>>((float*)dst, W, H, pitch, (float)value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_draw_line(int prec, void* phi, int W, int H, int64_t pitch, double x0,
+                             double y0, double x1, double y1, double width, double value,
+                             cudaStream_t st)
+{
+    const double h = 0.5 * width;
+    double lo_i = floor(fmin(y0, y1) - h) - 1.0, hi_i = ceil(fmax(y0, y1) + h) + 1.0;
+    double lo_j = floor(fmin(x0, x1) - h) - 1.0, hi_j = ceil(fmax(x0, x1) + h) + 1.0;
+    if (lo_i < 0.0) lo_i = 0.0;
+    if (lo_j < 0.0) lo_j = 0.0;
+    if (hi_i > H - 1) hi_i = H - 1;
+    if (hi_j > W - 1) hi_j = W - 1;
+    if (hi_i < lo_i || hi_j < lo_j) return cudaSuccess;  // misses the grid
+    const int i0 = (int)lo_i, j0 = (int)lo_j;
+    const int ni = (int)hi_i - i0 + 1, nj = (int)hi_j - j0 + 1;
+    const int t = 256;
+    const int b = grid_for((int64_t)ni * nj, t);
+    const double half2 = h * h;
+    if (prec == P_F64)
+        k_draw_line<double><<<b, t, 0, st>>>((double*)phi, W, H, pitch, i0, j0, ni, nj, x0, y0, x1, y1, half2, value);
+    else
+        k_draw_line<float><<<b, t, 0, st>>>((float*)phi, W, H, pitch, i0, j0, ni, nj, x0, y0, x1, y1, half2, (float)value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render(int prec, const void* u, const void* v, const void* phi,
+                          const float* tl, int W, int H, int64_t pitch, int64_t tl_pitch,
+                          float u_scale, float v_scale, double thr, void* out, cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    uchar4* o = (uchar4*)out;
+    switch (prec) {
+        case P_F32: k_render<float><<<b, t, 0, st>>>((const float*)u, (const float*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
+        case P_F64: k_render<double><<<b, t, 0, st>>>((const double*)u, (const double*)v, (const double*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
+        case P_BF16: k_render<__nv_bfloat16><<<b, t, 0, st>>>((const __nv_bfloat16*)u, (const __nv_bfloat16*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
+        case P_F16: k_render<__half><<<b, t, 0, st>>>((const __half*)u, (const __half*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_timelapse(int prec, const void* u, float* tl, int W, int H, int64_t pitch,
+                             int64_t tl_pitch, int reset, cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    switch (prec) {
+        case P_F32: k_timelapse<float><<<b, t, 0, st>>>((const float*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        case P_F64: k_timelapse<double><<<b, t, 0, st>>>((const double*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        case P_BF16: k_timelapse<__nv_bfloat16><<<b, t, 0, st>>>((const __nv_bfloat16*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        case P_F16: k_timelapse<__half><<<b, t, 0, st>>>((const __half*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

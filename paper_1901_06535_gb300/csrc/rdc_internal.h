@@ -119,6 +119,17 @@ cudaError_t launch_phi_in(int prec, int src_dtype, const void* src, void* dst,
 // phi plane := value (uniform map).
 cudaError_t launch_fill_phi(int prec, void* dst, int W, int H, int64_t pitch, double value,
                             cudaStream_t st);
+// phi := value for cells within width/2 of the segment (x0,y0)-(x1,y1).
+cudaError_t launch_draw_line(int prec, void* phi, int W, int H, int64_t pitch, double x0,
+                             double y0, double x1, double y1, double width, double value,
+                             cudaStream_t st);
+// RGBA8 image of the state (or of the timelapse plane tl when non-null).
+cudaError_t launch_render(int prec, const void* u, const void* v, const void* phi,
+                          const float* tl, int W, int H, int64_t pitch, int64_t tl_pitch,
+                          float u_scale, float v_scale, double thr, void* out, cudaStream_t st);
+// tl := reset ? u : max(tl, u), in FP32.
+cudaError_t launch_timelapse(int prec, const void* u, float* tl, int W, int H, int64_t pitch,
+                             int64_t tl_pitch, int reset, cudaStream_t st);
 // u at flat cell indices -> doubles.
 cudaError_t launch_probe(int prec, const void* u, int W, int64_t pitch,
                          const int64_t* cells, int n, double* out,

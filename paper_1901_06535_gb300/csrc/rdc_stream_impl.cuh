@@ -73,12 +73,16 @@ struct StreamGeom {
 // [y0, y1).  Warps are independent, so the same body serves one grid per
 // launch (k_stepk_stream) and a work list over many grids (k_stream_batch).
 //
-// Borders.  Rows: when a level produces row 0 it also writes that row into
-// its "row -1" register (the mirror ghost), and when it passes row H-1 it
-// produces a ghost row H equal to row H-1; the next level then reads its
-// north/south neighbours without any per-cell test.  Columns: only a warp
-// whose strip touches column 0 or W-1 (XE) tests columns per cell.
-template <typename S, int MODE, int K, int N, bool XE>
+// The row loop's body is straight-line code: every level computes its row
+// even when that row lies outside the grid (the phi load is clamped to a
+// real row), and the mirror borders are applied by selects.  Rows outside
+// the grid hold garbage that no valid cell ever reads: the select at rows
+// 0 and H-1 (and columns 0 and W-1) replaces the out-of-range neighbour by
+// the cell itself.  Straight-line code lets the compiler interleave the
+// levels' arithmetic; warp-uniform branches there measured slower.  For
+// K >= 5 the row loop is unrolled three times, which turns the three-row
+// register rotation into renaming.
+template <typename S, int MODE, int K, int N>
 __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                                                  const S* __restrict__ v,
                                                  const typename Traits<S>::PhiT* __restrict__ phi,
@@ -89,49 +93,34 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     using T = typename Traits<S>::T;
     using G = StreamGeom<S, K, N>;
     const int lane = threadIdx.x & 31;
-    const int a = col_out - G::HALO;                  // first column the warp holds
-    const int cl = a + lane * N;                      // first column of this lane
-    const bool in_grid = (cl >= 0) && (cl < W);       // vectors never straddle column 0
+    const int a = col_out - G::HALO;
+    const int cl = a + lane * N;
+    const bool in_grid = (cl >= 0) && (cl < W);
     const int t0 = max(y0 - K, 0);
-    const int t_end = y1 - 1 + K;                     // level K reaches row y1 - 1 here
-
-    // P*[l]: last three u rows of level l (P2 oldest); Q*[l]: last two v rows.
+    const int t_end = y1 - 1 + K;
     T P0[K][N], P1[K][N], P2[K][N], Q0[K][N], Q1[K][N];
 #pragma unroll
     for (int l = 0; l < K; ++l)
 #pragma unroll
         for (int e = 0; e < N; ++e) P0[l][e] = P1[l][e] = P2[l][e] = Q0[l][e] = Q1[l][e] = T(0);
-
+    constexpr int UNROLL = (K >= 5) ? 3 : 1;
+#pragma unroll UNROLL
     for (int t = t0; t <= t_end; ++t) {
-        // level 0: load row t (row H is the ghost copy of row H - 1)
         {
             T nu[N], nv[N];
 #pragma unroll
             for (int e = 0; e < N; ++e) nu[e] = nv[e] = T(0);
-            if (t < H) {
-                if (in_grid) {
-                    const int64_t o = (int64_t)t * pitch + cl;
-                    VecN<S, N>::load(u + o, nu);
-                    VecN<S, N>::load(v + o, nv);
-                }
-            } else if (t == H) {
-#pragma unroll
-                for (int e = 0; e < N; ++e) nu[e] = P0[0][e];
+            if (t < H && in_grid) {
+                const int64_t o = (int64_t)t * pitch + cl;
+                VecN<S, N>::load(u + o, nu);
+                VecN<S, N>::load(v + o, nv);
             }
 #pragma unroll
             for (int e = 0; e < N; ++e) {
-                P2[0][e] = P1[0][e];
-                P1[0][e] = P0[0][e];
-                P0[0][e] = nu[e];
-                Q1[0][e] = Q0[0][e];
-                Q0[0][e] = nv[e];
-            }
-            if (t == 0) {
-#pragma unroll
-                for (int e = 0; e < N; ++e) P1[0][e] = P0[0][e];  // ghost row -1
+                P2[0][e] = P1[0][e]; P1[0][e] = P0[0][e]; P0[0][e] = nu[e];
+                Q1[0][e] = Q0[0][e]; Q0[0][e] = nv[e];
             }
         }
-        // levels 1..K: row r = t - l from rows r-1, r, r+1 of level l-1
 #pragma unroll
         for (int l = 1; l <= K; ++l) {
             const int r = t - l;
@@ -139,56 +128,39 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
             T nu[N], nv[N];
             const T wsh = __shfl_up_sync(0xffffffffu, P1[l - 1][N - 1], 1);
             const T esh = __shfl_down_sync(0xffffffffu, P1[l - 1][0], 1);
-            if (live) {
+            {
                 T ph[N];
+                const int rc = min(max(r, 0), H - 1);   // rows outside the grid compute garbage
                 if (in_grid) {
-                    VecN<typename Traits<S>::PhiT, N>::load(phi + (int64_t)r * pitch + cl, ph);
+                    VecN<typename Traits<S>::PhiT, N>::load(phi + (int64_t)rc * pitch + cl, ph);
                 } else {
 #pragma unroll
                     for (int e = 0; e < N; ++e) ph[e] = T(0);
                 }
+                const bool top = (r == 0), bottom = (r == H - 1);
 #pragma unroll
                 for (int e = 0; e < N; ++e) {
+                    const int col = cl + e;
                     const T c = P1[l - 1][e];
                     T w = (e == 0) ? wsh : P1[l - 1][e - 1];
                     T ea = (e == N - 1) ? esh : P1[l - 1][e + 1];
-                    if (XE) {
-                        const int col = cl + e;
-                        if (col <= 0) w = c;          // mirror at the west border
-                        if (col >= W - 1) ea = c;     // mirror at the east border
-                    }
+                    if (col <= 0) w = c;
+                    if (col >= W - 1) ea = c;
+                    const T n = top ? c : P2[l - 1][e];
+                    const T s = bottom ? c : P0[l - 1][e];
                     T un, vn;
-                    cell_update<MODE>(c, w, ea, P2[l - 1][e], P0[l - 1][e], Q1[l - 1][e], ph[e],
-                                      m, un, vn);
+                    cell_update<MODE>(c, w, ea, n, s, Q1[l - 1][e], ph[e], m, un, vn);
                     nu[e] = quantize<S>(un);
                     nv[e] = quantize<S>(vn);
                 }
-            } else if (r == H && l < K) {
-#pragma unroll
-                for (int e = 0; e < N; ++e) {   // ghost row H of level l
-                    nu[e] = P0[l][e];
-                    nv[e] = T(0);
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < N; ++e) nu[e] = nv[e] = T(0);
             }
             if (l < K) {
 #pragma unroll
                 for (int e = 0; e < N; ++e) {
-                    P2[l][e] = P1[l][e];
-                    P1[l][e] = P0[l][e];
-                    P0[l][e] = nu[e];
-                    Q1[l][e] = Q0[l][e];
-                    Q0[l][e] = nv[e];
-                }
-                if (r == 0) {
-#pragma unroll
-                    for (int e = 0; e < N; ++e) P1[l][e] = P0[l][e];  // ghost row -1
+                    P2[l][e] = P1[l][e]; P1[l][e] = P0[l][e]; P0[l][e] = nu[e];
+                    Q1[l][e] = Q0[l][e]; Q0[l][e] = nv[e];
                 }
             } else if (live && r >= y0 && r < y1) {
-                // level K: write this lane's vector if it lies in the warp's
-                // interior columns and inside the grid
                 if (cl >= col_out && cl < col_out + G::OUTC && cl < W) {
                     const int64_t o = (int64_t)r * pitch + cl;
                     if (cl + N <= W) {
@@ -197,10 +169,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                     } else {
 #pragma unroll
                         for (int e = 0; e < N; ++e)
-                            if (cl + e < W) {
-                                u1[o + e] = narrow<S>(nu[e]);
-                                v1[o + e] = narrow<S>(nv[e]);
-                            }
+                            if (cl + e < W) { u1[o + e] = narrow<S>(nu[e]); v1[o + e] = narrow<S>(nv[e]); }
                     }
                 }
             }
@@ -215,13 +184,7 @@ __device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __
                                             int H, int64_t pitch, int col_out, int y0, int y1,
                                             const Model<typename Traits<S>::T>& m)
 {
-    using G = StreamGeom<S, K, N>;
-    const int a = col_out - G::HALO;
-    const bool edge = (a <= 0) || (a + G::WCOLS - 1 >= W - 1);   // warp-uniform
-    if (edge)
-        stream_warp_impl<S, MODE, K, N, true>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
-    else
-        stream_warp_impl<S, MODE, K, N, false>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
+    stream_warp_impl<S, MODE, K, N>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
 }
 
 template <typename S, int MODE, int K, int N>

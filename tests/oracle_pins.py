@@ -285,7 +285,48 @@ def pin_health(o, om):
     assert r["status"] == 0 and r["bad_step"] == -1
 
 
+def pin_render(o, om):
+    """§3.1: red carries u, blue carries v, green marks inhibitive substrate;
+    values are clamped to [0, 1] and coded to 0..255 with ties to even."""
+    u = np.array([[1.0, 0.0, 0.5, 2.0, -1.0, 127.5 / 255, 128.5 / 255]], dtype=np.float32)
+    v = np.array([[0.0, 1.0, 0.25, -3.0, 9.0, 0.0, 0.0]], dtype=np.float32)
+    phi = np.array([[0.054, 0.2, 0.0975, 0.054, 0.2, 0.054, 0.054]])
+    img = o.render(u, v, phi, 1.0, 1.0, thr=0.07575)
+    assert img[0, 0].tolist() == [255, 0, 0, 255]        # pure u -> red
+    assert img[0, 1].tolist() == [0, 255, 255, 255]      # v, on substrate
+    assert img[0, 2].tolist() == [128, 255, 64, 255]     # 127.5 -> 128, 63.75 -> 64
+    assert img[0, 3].tolist() == [255, 0, 0, 255]        # clamped above / below
+    assert img[0, 4].tolist() == [0, 255, 255, 255]
+    assert img[0, 5, 0] == 128 and img[0, 6, 0] == 128   # ties to even: 127.5, 128.5
+    tl = o.timelapse(u)
+    tl = o.timelapse(np.zeros_like(u), tl)
+    tl = o.timelapse(np.full_like(u, 0.75), tl)
+    assert np.array_equal(tl, np.maximum(np.maximum(u, 0), 0.75).astype(np.float32))
+    img = o.render(u, v, phi, 1.0, 1.0, thr=0.07575, tl=tl)
+    assert (img[..., 2] == 0).all() and img[0, 1, 0] == 191   # 0.75 * 255 = 191.25
+
+
+def pin_draw(o, om):
+    """§3 line presets: a horizontal line centred between rows covers exactly
+    `width` rows (2, 3 centred on a row, 8); snapped segments lie on multiples
+    of 15 degrees and keep their length; a zero-length line is a disk."""
+    for width, yc in ((2, 10.5), (3, 10.0), (8, 10.5)):
+        phi = np.zeros((24, 40))
+        o.draw_line(phi, 5.0, yc, 30.0, yc, float(width), 1.0)
+        rows = np.nonzero(phi[:, 17])[0]
+        assert len(rows) == width, (width, rows)
+        assert phi[:, :5 - width // 2 - 1].sum() == 0        # ends are rounded caps
+    x1, y1 = o.snap_segment(0.0, 0.0, 10.0, 9.4, 15.0)     # 43.2 deg -> 45
+    assert abs(x1 - y1) < 1e-12 and abs(np.hypot(x1, y1) - np.hypot(10.0, 9.4)) < 1e-12
+    x1, y1 = o.snap_segment(3.0, 4.0, 20.0, 5.0, 15.0)     # 3.4 deg -> 0
+    assert y1 == 4.0 and abs(x1 - (3.0 + np.hypot(17.0, 1.0))) < 1e-12
+    x1, y1 = o.snap_segment(0.0, 0.0, -1.0, 10.0, 15.0)    # 95.7 deg -> 90
+    assert abs(x1) < 1e-12 and abs(y1 - np.hypot(1.0, 10.0)) < 1e-12
+    phi = np.zeros((21, 21))
+    assert o.draw_line(phi, 10.0, 10.0, 10.0, 10.0, 8.0, 1.0) == GAUSS_N[4]
+
+
 ALL_PINS = [pin_rest_root, pin_rest_fixed_point, pin_jacobian, pin_jacobian_with_mode,
             pin_cosine_modes,
             pin_conservation, pin_symmetry, pin_one_d, pin_uniform_is_single, pin_spike,
-            pin_gauss_circle, pin_health]
+            pin_gauss_circle, pin_health, pin_render, pin_draw]

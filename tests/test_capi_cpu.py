@@ -79,3 +79,9 @@ def test_create_validates_grid_and_phi(librdc):
 def test_status_strings(librdc):
     for code in range(8):
         assert librdc.rdc_status_str(code).startswith("RDC_")
+
+
+@pytest.mark.parametrize("seg", [(0, 0, 10, 9.4), (3, 4, 20, 5), (0, 0, -1, 10), (5.5, 7.25, -30, -2),
+                                 (100, 50, 60, 120), (1, 1, 1, 1)])
+def test_host_snap_segment_bitwise_vs_oracle(librdc, orc, seg):
+    assert librdc.rdc_snap_segment(*seg, 15.0) == orc.snap_segment(*seg, 15.0)

@@ -205,3 +205,32 @@ def test_batch_sweep_workload_small(gpu):
             assert np.array_equal(u, us)
     finally:
         gpu.rdc_batch_destroy(b)
+
+
+def test_sweep_grid_that_crosses_the_pole(gpu, orc, om):
+    """Grid 257 of the 512-grid sweep (256 x 256, eps = 0.02004, phi = 0.070)
+    overshoots past the pole u = -q in the wave tail: the FP64 oracle reports
+    it at step 419.  The FP64 GPU path is bit-identical, so its health flag
+    must be clear after 418 steps and raised after 419."""
+    spec = ri.sweep_batch(seed=4, n_grids=512)
+    i = 257
+    n = spec.sizes[i]
+    phi = np.full((n, n), float(np.float32(spec.phi[i])))
+    u0, v0 = orc.rest_field(phi)
+    for (cx, cy, r) in spec.disks[i]:
+        orc.seed_disk(u0, cx, cy, r, 0.8)
+    ref = orc.run(phi, u0, v0, 500, params=om.Params(eps=spec.eps[i]))
+    assert ref["status"] == om.ENONFINITE
+    bad_step = ref["bad_step"]
+    p = gpu.rdc_params_default(precision=1, eps=spec.eps[i], k_block=1)
+    h = gpu.rdc_create(n, n, p, phi)
+    try:
+        for (cx, cy, r) in spec.disks[i]:
+            gpu.rdc_seed(h, cx, cy, r, 0.8)
+        gpu.rdc_step(h, bad_step - 1)
+        assert gpu.rdc_check(h) == (0, -1)
+        gpu.rdc_step(h, 1)
+        rc, idx = gpu.rdc_check(h)
+        assert rc == gpu.RDC_ENONFINITE and idx == ref["bad_index"]
+    finally:
+        gpu.rdc_destroy(h)

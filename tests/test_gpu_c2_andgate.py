@@ -1,0 +1,71 @@
+"""The AND-gate workload at full size: 1024 x 1024, 20000 Euler steps, two
+16-cell input channels meeting head-on, a 3-cell semi-permeable band before
+the output channel, phi = 0.2 elsewhere, u = 0.8 input disks (§4.1).
+
+FP64 on the GPU is bit-identical to the oracle (tests/test_gpu_parity.py), so
+its truth table here is the oracle's; FP32 must give the same table and an
+output arrival within 1 % of FP64.  BF16 storage is run and reported."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import rdc_inputs as ri
+from tests.helpers import PREC, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+N, STEPS, SAMPLE = 1024, 20000, 50
+
+
+def _circuit():
+    return ri.and_gate(N, N, arm=150, out_len=80)
+
+
+def _max_at_output(pkg, c, fire, prec):
+    """Largest u seen at the output probe, sampled every SAMPLE steps."""
+    phi = c.phi if prec == "f64" else c.phi.astype(np.float32)
+    p = pkg.rdc_params_default(precision=PREC[prec], k_block=0 if prec != "f64" else 1)
+    h = pkg.rdc_create(N, N, p, phi)
+    best = -1.0
+    try:
+        for name in fire:
+            pkg.rdc_seed(h, *c.seeds[name], 0.8)
+        for _ in range(STEPS // SAMPLE):
+            pkg.rdc_step(h, SAMPLE)
+            best = max(best, float(pkg.rdc_probe(h, [c.probes["out"]])[0]))
+        assert pkg.rdc_check(h)[0] == pkg.RDC_OK
+    finally:
+        pkg.rdc_destroy(h)
+    return best
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_c2_truth_table(gpu, prec):
+    c = _circuit()
+    out = {tuple(f): _max_at_output(gpu, c, f, prec) > 0.3
+           for f in ([], ["A"], ["B"], ["A", "B"])}
+    assert out == {(): False, ("A",): False, ("B",): False, ("A", "B"): True}, out
+
+
+def test_c2_output_arrival_f32_vs_f64(gpu, record_property):
+    c = _circuit()
+    seeds = [(*c.seeds["A"], 0.8), (*c.seeds["B"], 0.8)]
+    t = {}
+    for prec in ("f64", "f32"):
+        phi = c.phi if prec == "f64" else c.phi.astype(np.float32)
+        _, _, ex = gpu_run(gpu, N, N, phi=phi, seeds=seeds, n=STEPS, prec=prec, k=1,
+                           probes=[c.probes["out"]])
+        t[prec] = float(ex["t_arr"][0])
+    record_property("t_out", t)
+    assert t["f64"] > 0 and abs(t["f32"] - t["f64"]) <= 0.01 * t["f64"], t
+
+
+def test_c2_bf16_reported(gpu, record_property):
+    """BF16 storage on the same circuit: reported, not gated (the gate's
+    window is about 2 % of the band's phi; BF16 shifts fronts by ~1 %)."""
+    c = _circuit()
+    table = {"".join(f) or "-": bool(_max_at_output(gpu, c, f, "bf16") > 0.3)
+             for f in ([], ["A"], ["B"], ["A", "B"])}
+    record_property("bf16_truth_table", table)
+    print("bf16 AND truth table at 1024^2:", table)

@@ -349,3 +349,31 @@ def test_create_ext_on_torch_memory(gpu):
     ref, _, _ = gpu_run(gpu, W, H, seeds=[(60.0, 30.0, 8.0, 0.8)], n=250, prec="f32",
                         dtype=np.float32)
     assert np.array_equal(uo, ref)
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_tune_keeps_state_and_bits(gpu, prec):
+    """rdc_tune never advances the state, and whatever it picks, stepping
+    gives the bits of one step per launch."""
+    W, H = 700, 333
+    seeds = _centre_seed(W, H)
+    p = gpu.rdc_params_default(precision=PREC[prec])
+    h = gpu.rdc_create(W, H, p)
+    try:
+        for sd in seeds:
+            gpu.rdc_seed(h, *sd)
+        gpu.rdc_step(h, 10)
+        a = np.empty((H, W))
+        gpu.rdc_read(h, a, None)
+        shape, gcups = gpu.rdc_tune(h, 2)
+        assert gcups > 0 and 1 <= shape["k"] <= 8
+        b = np.empty((H, W))
+        gpu.rdc_read(h, b, None)
+        assert np.array_equal(a, b)
+        gpu.rdc_step(h, 37)
+        c = np.empty((H, W))
+        gpu.rdc_read(h, c, None)
+    finally:
+        gpu.rdc_destroy(h)
+    ref, _, _ = gpu_run(gpu, W, H, seeds=seeds, n=47, prec=prec, k=1)
+    assert np.array_equal(c, ref)
