@@ -101,6 +101,7 @@ k_step1(const S* __restrict__ u, const S* __restrict__ v,
         Model<typename Traits<S>::T> m)
 {
     constexpr int VEC = Traits<S>::VEC;
+    pdl_enter();
     const int wcol0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * VEC;
     const int row0 = blockIdx.y * rows;
     step1_warp<S, MODE>(u, v, phi, u1, v1, W, H, pitch, wcol0, row0, min(row0 + rows, H), m);
@@ -129,6 +130,7 @@ k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
+    pdl_enter();
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
         const Item item = items[it];
@@ -148,8 +150,7 @@ cudaError_t launch_batch_step1_t(const GridDesc* d, const Item* items, int nitem
 {
     if (nitems <= 0) return cudaSuccess;
     if (ctas < 1) return cudaErrorInvalidValue;
-    k_step1_batch<S><<<ctas, 128, 0, st>>>(d, items, nitems, j);
-    return cudaGetLastError();
+    return launch_pdl(k_step1_batch<S>, dim3(ctas), dim3(128), 0, st, d, items, nitems, j);
 }
 
 // Shared-memory layout of k_stepk: four planes of (tx+2k) x (ty+2k) compute
@@ -266,20 +267,19 @@ cudaError_t launch_step1_t(int mode, const Planes& g, const ModelD& md, Shape1 s
     const PhiT* phi = static_cast<const PhiT*>(g.phi);
     S* u1 = static_cast<S*>(g.u1);
     S* v1 = static_cast<S*>(g.v1);
+    const dim3 block(sh.bx);
     switch (mode) {
         case MODE_FULL:
-            k_step1<S, MODE_FULL><<<grid, sh.bx, 0, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, rows, m);
-            break;
+            return launch_pdl(k_step1<S, MODE_FULL>, grid, block, 0, st, u, v, phi, u1, v1, g.W,
+                              g.H, g.pitch, rows, m);
         case MODE_DIFFUSION:
-            k_step1<S, MODE_DIFFUSION><<<grid, sh.bx, 0, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, rows, m);
-            break;
+            return launch_pdl(k_step1<S, MODE_DIFFUSION>, grid, block, 0, st, u, v, phi, u1, v1,
+                              g.W, g.H, g.pitch, rows, m);
         case MODE_REACTION:
-            k_step1<S, MODE_REACTION><<<grid, sh.bx, 0, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, rows, m);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+            return launch_pdl(k_step1<S, MODE_REACTION>, grid, block, 0, st, u, v, phi, u1, v1,
+                              g.W, g.H, g.pitch, rows, m);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 template <typename S>

@@ -195,6 +195,7 @@ k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
                Model<typename Traits<S>::T> m)
 {
     using G = StreamGeom<S, K, N>;
+    pdl_enter();
     const int wx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wx >= nwarps_x) return;                       // whole warps only
     const int y0 = blockIdx.y * rows;
@@ -210,6 +211,7 @@ k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ item
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
+    pdl_enter();
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
         const Item item = items[it];
@@ -243,11 +245,10 @@ cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>&
     const int wpb = 4;
     if ((g.H + rows - 1) / rows > 65535) return cudaErrorInvalidValue;
     dim3 grid((nwx + wpb - 1) / wpb, (g.H + rows - 1) / rows);
-    k_stepk_stream<S, MODE_FULL, K, N><<<grid, 32 * wpb, 0, st>>>(
-        static_cast<const S*>(g.u), static_cast<const S*>(g.v),
-        static_cast<const PhiT*>(g.phi), static_cast<S*>(g.u1), static_cast<S*>(g.v1), g.W,
-        g.H, g.pitch, rows, nwx, m);
-    return cudaGetLastError();
+    return launch_pdl(k_stepk_stream<S, MODE_FULL, K, N>, grid, dim3(32 * wpb), 0, st,
+                      static_cast<const S*>(g.u), static_cast<const S*>(g.v),
+                      static_cast<const PhiT*>(g.phi), static_cast<S*>(g.u1),
+                      static_cast<S*>(g.v1), g.W, g.H, g.pitch, rows, nwx, m);
 }
 
 template <typename S, int K>
@@ -255,8 +256,7 @@ cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nite
                                   int ctas, cudaStream_t st)
 {
     constexpr int N = StreamVec<S, K>::N;
-    k_stream_batch<S, K, N><<<ctas, 128, 0, st>>>(d, items, nitems, j);
-    return cudaGetLastError();
+    return launch_pdl(k_stream_batch<S, K, N>, dim3(ctas), dim3(128), 0, st, d, items, nitems, j);
 }
 
 template <typename S>

@@ -85,3 +85,12 @@ def test_status_strings(librdc):
                                  (100, 50, 60, 120), (1, 1, 1, 1)])
 def test_host_snap_segment_bitwise_vs_oracle(librdc, orc, seg):
     assert librdc.rdc_snap_segment(*seg, 15.0) == orc.snap_segment(*seg, 15.0)
+
+
+def test_missing_library_fails_loudly(librdc, monkeypatch, tmp_path):
+    """Without the built library the binding raises; there is no fallback."""
+    from paper_1901_06535_gb300 import _capi
+    monkeypatch.setattr(_capi._build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_capi, "_LIB", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _capi.lib()
