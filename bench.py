@@ -437,12 +437,12 @@ def _batch_sweep(pkg, stream, steps=5000):
         z.record(stream)
         torch.cuda.synchronize()
         sec = a.elapsed_time(z) / 1e3
-        bad = sum(pkg.rdc_batch_check(b, i)[0] != 0 for i in range(len(grids)))
+        bad = [i for i in range(len(grids)) if pkg.rdc_batch_check(b, i)[0] != 0]
         cells = float(sum(n * n for n in spec.sizes))
         return {"gcups": cells * steps / sec / 1e9, "seconds": sec, "grids": len(grids),
                 "cells": cells, "steps": steps, "k": info.k, "rows": info.rows,
                 "krows": info.krows, "tuned_gcups": info.tuned_gcups,
-                "tune_seconds": tune_s, "unhealthy_grids": int(bad)}
+                "tune_seconds": tune_s, "unhealthy_grids": bad}
     finally:
         pkg.rdc_batch_destroy(b)
 

@@ -189,11 +189,16 @@ int rdc_set_state(rdc_sim* sim, const void* u_host, const void* v_host,
  *     u'  = c + dt * (R/eps + Du*lap)     (flags drop one of the two terms)
  *     v'  = v + dt * (c - v)
  * RDC_F64 evaluates exactly this sequence in FP64 with IEEE division and no
- * fused multiply-add.  The FP32 modes evaluate it in FP32: rat with IEEE
- * division, R/eps as R times 1/eps (rounded once to FP32, as Eq. 1 writes the
- * bracket scaled by 1/eps) fused with Du*lap, a fixed set of fused
- * multiply-adds elsewhere; u', v' are rounded to the storage type after every
- * step.  Every k_block and launch shape gives the same bits.
+ * fused multiply-add.  The FP32 modes evaluate, in FP32 with round-to-nearest
+ * and with a = dt Du / dx^2 and b = dt / eps each computed in FP64 and rounded
+ * once to FP32 (Eq. 1 scales the bracket by 1/eps):
+ *     rat = (c - q) / (c + q)                      (IEEE division)
+ *     R   = fma(-fma(f, v, phi), rat, fma(-c, c, c))
+ *     u'  = fma(R, b, fma(fma(-4, c, (w + e) + (n_ + s)), a, c))
+ *     v'  = fma(dt, c - v, v)
+ * (the flags drop the first or the second fma of u'); u', v' are rounded to
+ * the storage type after every step.  Every k_block and launch shape gives
+ * the same bits.
  */
 int rdc_step(rdc_sim* sim, int64_t n);
 

@@ -181,6 +181,9 @@ int host_cuda_fail(cudaError_t e, const char* what)
 {
     std::snprintf(g_err, sizeof g_err, "%s: %s (%s)", what, cudaGetErrorName(e),
                   cudaGetErrorString(e));
+    // A failed runtime call leaves its (non-sticky) error as the "last error";
+    // clear it so that the next kernel launch does not report it as its own.
+    (void)cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? RDC_ENOMEM : RDC_ECUDA;
 }
 
@@ -875,9 +878,10 @@ int rdc_tune(rdc_sim* s, int32_t reps, rdc_launch_shape* out, double* best_gcups
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "cudaEventCreate");
-    if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaError_t ee = cudaEventCreate(&e1);
+    if (ee != cudaSuccess) {
         cudaEventDestroy(e0);
-        return RDC_ECUDA;
+        return host_cuda_fail(ee, "cudaEventCreate");
     }
     double best = -1.0;
     Cand pick{s->shapek.k > 1, s->shape1, s->shapek};

@@ -587,10 +587,12 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
     int rc = upload_desc(b);
     if (rc) return rc;
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return RDC_ECUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaError_t ee = cudaEventCreate(&e0);
+    if (ee != cudaSuccess) return host_cuda_fail(ee, "cudaEventCreate");
+    ee = cudaEventCreate(&e1);
+    if (ee != cudaSuccess) {
         cudaEventDestroy(e0);
-        return RDC_ECUDA;
+        return host_cuda_fail(ee, "cudaEventCreate");
     }
     const Config saved = b->cfg;
     Config best = saved;

@@ -31,19 +31,27 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;
 void* g_scratch_addr[64] = {nullptr};   // device address of g_scratch, per device
 
+// RDC_ECUDA, after clearing the failed call's error from the runtime's
+// last-error state (so that a later launch does not report it).
+int cuda_error()
+{
+    (void)cudaGetLastError();
+    return RDC_ECUDA;
+}
+
 // Device address of g_scratch on the current device, looked up once per device
 // with that device current.
 int scratch_address(void** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return RDC_ECUDA;
+    if (e != cudaSuccess) return cuda_error();
     if (dev < 0 || dev >= 64) return RDC_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return RDC_ECUDA;
+        if (e != cudaSuccess) return cuda_error();
         g_scratch_addr[dev] = p;
     }
     *out = g_scratch_addr[dev];
@@ -66,6 +74,7 @@ bool params_ok(const rdc_params* p)
 }
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
 
 }  // namespace
 
@@ -128,7 +137,7 @@ extern "C" int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_i
         if (e == cudaSuccess)
             e = cudaMemcpy2DAsync(v_out, pitch_bytes, v_in, pitch_bytes,
                                   (size_t)g.width * esz, g.height, cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return RDC_ECUDA;
+        if (e != cudaSuccess) return cuda_error();
     } else {
         // Launch j of L writes the output buffers when L - j is even and the
         // scratch pair otherwise, so the last launch lands in the output.
@@ -149,7 +158,7 @@ extern "C" int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_i
                 e = launch_step1(prec, p->flags, pl, m, s1, st);
                 left -= 1;
             }
-            if (e != cudaSuccess) return RDC_ECUDA;
+            if (e != cudaSuccess) return cuda_error();
             cu = du;
             cv = dv;
         }
@@ -163,7 +172,7 @@ extern "C" int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_i
     unsigned long long h = ~0ull;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof h, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return RDC_ECUDA;
+    if (e != cudaSuccess) return cuda_error();
     if (h != ~0ull) {
         *first_bad = (int64_t)h;
         return RDC_ENONFINITE;

@@ -93,8 +93,10 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
     }
 }
 
+// At most 72 registers: the 16-bit-storage instantiations (8 cells per
+// thread) would otherwise take 73 and fit one CTA fewer per SM.
 template <typename S, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __maxnreg__(72)
 k_step1(const S* __restrict__ u, const S* __restrict__ v,
         const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
         S* __restrict__ v1, int W, int H, int64_t pitch, int rows,
@@ -117,7 +119,8 @@ __device__ __forceinline__ Model<T> model_of(const GridDesc& d)
     m.Du = (T)d.Du;
     m.dt = (T)d.dt;
     m.inv_dx2 = (T)d.inv_dx2;
-    m.inv_eps = (T)(1.0 / d.eps);
+    m.dt_Dux = (T)(__dmul_rn(__dmul_rn(d.dt, d.Du), d.inv_dx2));
+    m.dt_eps = (T)(__ddiv_rn(d.dt, d.eps));
     return m;
 }
 
@@ -245,7 +248,8 @@ Model<typename Traits<S>::T> make_model(const ModelD& d)
     m.Du = (T)d.Du;
     m.dt = (T)d.dt;
     m.inv_dx2 = (T)d.inv_dx2;
-    m.inv_eps = (T)(1.0 / d.eps);
+    m.dt_Dux = (T)((d.dt * d.Du) * d.inv_dx2);
+    m.dt_eps = (T)(d.dt / d.eps);
     return m;
 }
 

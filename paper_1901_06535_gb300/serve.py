@@ -91,6 +91,7 @@ class Server:
         self.ticks = 0
         self.cells_stepped = 0.0
         self.peak_sessions = 0
+        self.evicted = 0
 
     # -- sessions -------------------------------------------------------------
     def arrive(self, s: Session, now: float | None = None):
@@ -159,6 +160,8 @@ class Server:
             if ev.query():
                 now = time.perf_counter()
                 for f in frames:
+                    if f.sid not in self.active:      # evicted while in flight
+                        continue
                     f.completed = now
                     self.completed.append(f)
                     s = self.active[f.sid]
@@ -172,6 +175,25 @@ class Server:
                 still.append((ev, frames))
         self.inflight = still
         return n
+
+    def evict(self, sid: int) -> bool:
+        """Drops a session at once (a client that went away): its pending or
+        in-flight frame is discarded and its memory freed; the other
+        sessions are unaffected.  Returns False if the session is unknown."""
+        if sid in self.pending:
+            del self.pending[sid]
+        for _, frames in self.inflight:
+            frames[:] = [f for f in frames if f.sid != sid]
+        if sid in self.active:
+            self._leave(self.active[sid])
+            self.evicted += 1
+            return True
+        for s in list(self.waiting):
+            if s.sid == sid:
+                self.waiting.remove(s)
+                self.evicted += 1
+                return True
+        return False
 
     def idle(self) -> bool:
         return not (self.waiting or self.active or self.inflight)
@@ -194,7 +216,7 @@ class Server:
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "max_ms": float(lat.max()) if len(lat) else None,
                 "ticks": self.ticks, "cells_stepped": self.cells_stepped,
-                "peak_sessions": self.peak_sessions}
+                "peak_sessions": self.peak_sessions, "evicted": self.evicted}
 
 
 def run_workload(sessions, arrivals, server: Server, poll_sleep: float = 50e-6,

@@ -377,3 +377,22 @@ def test_tune_keeps_state_and_bits(gpu, prec):
         gpu.rdc_destroy(h)
     ref, _, _ = gpu_run(gpu, W, H, seeds=seeds, n=47, prec=prec, k=1)
     assert np.array_equal(c, ref)
+
+
+def test_allocation_failure_is_reported_and_recoverable(gpu):
+    """A grid larger than device memory: cudaMalloc fails, the call returns
+    RDC_ENOMEM (no handle), and the library keeps working."""
+    p = gpu.rdc_params_default(precision=0)
+    with pytest.raises(gpu.RdcError) as e:
+        gpu.rdc_create(200000, 200000, p)          # 40 G cells x 20 B = 800 GB
+    assert e.value.status == gpu.RDC_ENOMEM
+    b = gpu.rdc_batch_create([], [p])
+    try:
+        with pytest.raises(gpu.RdcError) as e:
+            gpu.rdc_batch_add(b, 200000, 200000, p)
+        assert e.value.status == gpu.RDC_ENOMEM
+        assert gpu.rdc_batch_get_info(b).ngrids == 0
+    finally:
+        gpu.rdc_batch_destroy(b)
+    u, _, _ = gpu_run(gpu, 40, 30, seeds=[(20, 15, 4, 0.8)], n=5, prec="f32")
+    assert np.isfinite(u).all()

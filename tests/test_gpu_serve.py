@@ -98,3 +98,41 @@ def test_serving_overlapping_arrivals(gpu):
         u, _ = finals[s.sid]
         ua, _ = _alone(gpu, s, 16)
         assert np.array_equal(u, ua)
+
+
+def test_serving_eviction_mid_stream(gpu):
+    """A session dropped while its frame is in flight frees its memory; the
+    remaining sessions finish with the same bits as alone."""
+    from paper_1901_06535_gb300 import serve
+    sessions = _sessions(serve, 6, seed=21, frames=5)
+    srv = serve.Server(precision=0, k_block=2, steps_per_frame=12)
+    finals = {}
+    orig_leave = srv._leave
+
+    def leave(s):
+        if s.done_frames >= s.frames:
+            finals[s.sid] = srv.read(s)
+        orig_leave(s)
+
+    srv._leave = leave
+    try:
+        for s in sessions:
+            srv.arrive(s)
+        srv.tick()                                  # all six frames in flight
+        used_before = srv.used
+        assert srv.evict(sessions[2].sid)           # dropped mid-stream
+        assert srv.used < used_before and sessions[2].sid not in srv.active
+        while not srv.idle():
+            srv.poll()
+            if not srv.tick():
+                srv.torch.cuda.synchronize()
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["evicted"] == 1 and sessions[2].sid not in finals
+    for s in sessions:
+        if s.sid == sessions[2].sid:
+            continue
+        u, v = finals[s.sid]
+        ua, va = _alone(gpu, s, 12)
+        assert np.array_equal(u, ua) and np.array_equal(v, va), s.sid
