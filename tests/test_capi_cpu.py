@@ -94,3 +94,23 @@ def test_missing_library_fails_loudly(librdc, monkeypatch, tmp_path):
     monkeypatch.setattr(_capi, "_LIB", None)
     with pytest.raises(RuntimeError, match="not built"):
         _capi.lib()
+
+
+def test_create_ext_validates_before_touching_the_device(librdc):
+    """Misaligned pointers, bad pitches and missing planes are refused with
+    RDC_EINVAL before any device call (fake, never dereferenced addresses)."""
+    p = librdc.rdc_params_default()
+    base = 1 << 40
+    good_u, good_v = [base, base + 4096], [base + 8192, base + 12288]
+    phi = base + 16384
+    cases = [
+        dict(u=[base + 4, base + 4096], v=good_v, phi=phi, pitch=256),   # misaligned u
+        dict(u=good_u, v=good_v, phi=phi + 8, pitch=256),                # misaligned phi
+        dict(u=good_u, v=good_v, phi=phi, pitch=100),                    # pitch not 16-aligned
+        dict(u=good_u, v=good_v, phi=phi, pitch=32),                     # pitch < W * 4
+        dict(u=[0, base], v=good_v, phi=phi, pitch=256),                 # null plane
+    ]
+    for c in cases:
+        with pytest.raises(librdc.RdcError) as e:
+            librdc.rdc_create_ext(16, 4, p, c["u"], c["v"], c["phi"], c["pitch"])
+        assert e.value.status == librdc.RDC_EINVAL
