@@ -192,13 +192,15 @@ int rdc_set_state(rdc_sim* sim, const void* u_host, const void* v_host,
  * fused multiply-add.  The FP32 modes evaluate, in FP32 with round-to-nearest
  * and with a = dt Du / dx^2 and b = dt / eps each computed in FP64 and rounded
  * once to FP32 (Eq. 1 scales the bracket by 1/eps):
- *     rat = (c - q) / (c + q)                      (IEEE division)
+ *     rat = (c - q) / (c + q)    (the correctly rounded quotient, as IEEE
+ *                                 division gives it: see rdc_check_division)
  *     R   = fma(-fma(f, v, phi), rat, fma(-c, c, c))
  *     u'  = fma(R, b, fma(fma(-4, c, (w + e) + (n_ + s)), a, c))
  *     v'  = fma(dt, c - v, v)
- * (the flags drop the first or the second fma of u'); u', v' are rounded to
- * the storage type after every step.  Every k_block and launch shape gives
- * the same bits.
+ * (the flags drop the first or the second fma of u'; the kernels form R and
+ * c - v with their signs flipped, which changes at most the sign of an exact
+ * zero); u', v' are rounded to the storage type after every step.  Every
+ * k_block and launch shape gives the same bits.
  */
 int rdc_step(rdc_sim* sim, int64_t n);
 
@@ -507,6 +509,39 @@ int rdc_batch_get_info(rdc_batch* b, rdc_batch_info* out);
  * the spare ones, so tuning does not advance or change any grid's state.
  */
 int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out);
+
+/* ---- diagnostics --------------------------------------------------------- */
+/*
+ * The paper has no counterpart: a self-check of this library's arithmetic.
+ * The FP32 modes compute the ratio (c - q)/(c + q) of rdc_step with a refined
+ * hardware reciprocal and one Markstein correction of the quotient (P.
+ * Markstein, IBM J. Res. Dev. 34(1), 1990) instead of the compiler's division
+ * sequence.  That yields the IEEE-754 round-to-nearest quotient whenever the
+ * refined reciprocal is itself correctly rounded.  This call checks, on the
+ * current device and bit for bit against the CUDA runtime's IEEE intrinsics:
+ *   [0] the refined reciprocal of every b = 2^e (1 + m 2^-23) with e in
+ *       [-125, 125] (every significand; b and 1/b normal);
+ *   [1] the ratio, in the scalar and the paired form the kernels use, for
+ *       every FP32 c with 0 < c + q < 2^126, q rounded to FP32 as the kernels
+ *       round it (about 2.1e9 values for q = 0.002; beyond 2^126 the
+ *       reciprocal estimate flushes the subnormal 1/(c + q) to zero, where
+ *       c*c has long overflowed and the state is non-finite anyway);
+ *   [2] a / b for n_random pairs of random normal floats (exponents in
+ *       [-60, 60], random signs; a SplitMix64 stream from seed); 0 skips it.
+ * out->checked[i] and out->mismatches[i] count the values of part i;
+ * out->first_bad[i] is the smallest offending bit pattern of b [0] or c [1],
+ * or the smallest offending pair index [2]; 0xffffffff when there is none.
+ * Synchronous (tens of milliseconds); allocates and frees a few bytes of
+ * device memory.  RDC_EINVAL: out NULL, or q not a finite value > 0.
+ */
+typedef struct {
+    uint64_t checked[3];
+    uint64_t mismatches[3];
+    uint32_t first_bad[3];
+    uint32_t reserved;
+} rdc_division_report;
+
+int rdc_check_division(double q, uint64_t n_random, uint64_t seed, rdc_division_report* out);
 
 /* Human-readable name of a status code (static storage). */
 const char* rdc_status_str(int status);

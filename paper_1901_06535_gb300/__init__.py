@@ -24,7 +24,8 @@ from ._capi import (  # noqa: F401  (re-exported C-ABI names)
     rdc_batch_set_state, rdc_batch_step, rdc_batch_sync, rdc_batch_tune,
     RDC_RENDER_SNAPSHOT, RDC_RENDER_TIMELAPSE, rdc_render, rdc_timelapse_record, rdc_tune,
     RDC_SNAP_DEGREES, RDC_WIDTH_IMPERMEABLE, RDC_WIDTH_PERMEABLE, RDC_WIDTH_SEMIPERMEABLE,
-    rdc_draw_line, rdc_fill_phi, rdc_read_phi, rdc_snap_segment)
+    rdc_draw_line, rdc_fill_phi, rdc_read_phi, rdc_snap_segment, rdc_check_division,
+    rdc_division_report)
 
 
 class Sim:

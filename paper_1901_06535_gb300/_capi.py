@@ -88,6 +88,15 @@ class rdc_batch_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class rdc_division_report(ctypes.Structure):
+    _fields_ = [("checked", ctypes.c_uint64 * 3), ("mismatches", ctypes.c_uint64 * 3),
+                ("first_bad", ctypes.c_uint32 * 3), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"checked": list(self.checked), "mismatches": list(self.mismatches),
+                "first_bad": list(self.first_bad)}
+
+
 class RdcError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -155,6 +164,8 @@ _SIGS = {
     "rdc_render": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                   ctypes.c_double, _P, ctypes.c_int32]),
     "rdc_timelapse_record": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "rdc_check_division": (ctypes.c_int, [ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.POINTER(rdc_division_report)]),
     "rdc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "rdc_last_error": (ctypes.c_char_p, []),
 }
@@ -376,6 +387,15 @@ def rdc_get_view(h) -> rdc_view:
     v = rdc_view()
     _chk(lib().rdc_get_view(h, ctypes.byref(v)), "rdc_get_view")
     return v
+
+
+def rdc_check_division(q: float = 0.002, n_random: int = 1 << 26, seed: int = 1) -> dict:
+    """Exhaustive device check of the FP32 division used by the kernels
+    (see include/rdc.h); returns checked / mismatches / first_bad per part."""
+    rep = rdc_division_report()
+    _chk(lib().rdc_check_division(float(q), int(n_random), int(seed), ctypes.byref(rep)),
+         "rdc_check_division")
+    return rep.as_dict()
 
 
 def rdc_step_noalloc(width: int, height: int, params: rdc_params, u_in: int, v_in: int,

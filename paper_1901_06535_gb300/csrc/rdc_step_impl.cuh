@@ -65,12 +65,34 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
         if (lane != 31) er = esh;
         if (act) {
             T ou[VEC], ov[VEC];
+            if constexpr (sizeof(T) == 4) {
+                // FP32 compute: neighbouring cells in pairs (cell_update2)
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) {
-                const T w = (e == 0) ? wl : uc[e - 1];
-                T ea = (e == VEC - 1) ? er : uc[e + 1];
-                if (col0 + e >= W - 1) ea = uc[e];  // mirror at the east border
-                cell_update<MODE>(uc[e], w, ea, un[e], us[e], vv[e], ph[e], m, ou[e], ov[e]);
+                for (int e = 0; e < VEC; e += 2) {
+                    const float c0 = uc[e], c1 = uc[e + 1];
+                    const float2 w2 = make_float2((e == 0) ? wl : uc[e - 1], c0);
+                    const float2 e2 = make_float2(col0 + e >= W - 1 ? c0 : c1,
+                                                  col0 + e + 1 >= W - 1
+                                                      ? c1
+                                                      : ((e + 2 == VEC) ? er : uc[e + 2]));
+                    float2 o2, p2;
+                    cell_update2<MODE>(make_float2(c0, c1), w2, e2, make_float2(un[e], un[e + 1]),
+                                       make_float2(us[e], us[e + 1]),
+                                       make_float2(vv[e], vv[e + 1]),
+                                       make_float2(ph[e], ph[e + 1]), m, o2, p2);
+                    ou[e] = o2.x;
+                    ou[e + 1] = o2.y;
+                    ov[e] = p2.x;
+                    ov[e + 1] = p2.y;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    const T w = (e == 0) ? wl : uc[e - 1];
+                    T ea = (e == VEC - 1) ? er : uc[e + 1];
+                    if (col0 + e >= W - 1) ea = uc[e];  // mirror at the east border
+                    cell_update<MODE>(uc[e], w, ea, un[e], us[e], vv[e], ph[e], m, ou[e], ov[e]);
+                }
             }
             if (col0 + VEC <= W) {
                 Vec<S>::store(u1 + ro + col0, ou);

@@ -138,20 +138,47 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                     for (int e = 0; e < N; ++e) ph[e] = T(0);
                 }
                 const bool top = (r == 0), bottom = (r == H - 1);
+                if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+                    // FP32 compute: neighbouring cells in pairs (cell_update2).
+                    // The border selects also assemble the west and east pairs.
 #pragma unroll
-                for (int e = 0; e < N; ++e) {
-                    const int col = cl + e;
-                    const T c = P1[l - 1][e];
-                    T w = (e == 0) ? wsh : P1[l - 1][e - 1];
-                    T ea = (e == N - 1) ? esh : P1[l - 1][e + 1];
-                    if (col <= 0) w = c;
-                    if (col >= W - 1) ea = c;
-                    const T n = top ? c : P2[l - 1][e];
-                    const T s = bottom ? c : P0[l - 1][e];
-                    T un, vn;
-                    cell_update<MODE>(c, w, ea, n, s, Q1[l - 1][e], ph[e], m, un, vn);
-                    nu[e] = quantize<S>(un);
-                    nv[e] = quantize<S>(vn);
+                    for (int e = 0; e < N; e += 2) {
+                        const int col = cl + e;
+                        const float c0 = P1[l - 1][e], c1 = P1[l - 1][e + 1];
+                        const float wr = (e == 0) ? wsh : P1[l - 1][e - 1];
+                        const float er = (e + 2 == N) ? esh : P1[l - 1][e + 2];
+                        const float2 c2 = make_float2(c0, c1);
+                        const float2 w2 = make_float2(col <= 0 ? c0 : wr, col + 1 <= 0 ? c1 : c0);
+                        const float2 e2 = make_float2(col >= W - 1 ? c0 : c1,
+                                                      col + 1 >= W - 1 ? c1 : er);
+                        const float2 n2 = top ? c2 : make_float2(P2[l - 1][e], P2[l - 1][e + 1]);
+                        const float2 s2 =
+                            bottom ? c2 : make_float2(P0[l - 1][e], P0[l - 1][e + 1]);
+                        float2 un, vn;
+                        cell_update2<MODE>(c2, w2, e2, n2, s2,
+                                           make_float2(Q1[l - 1][e], Q1[l - 1][e + 1]),
+                                           make_float2(ph[e], ph[e + 1]), m, un, vn);
+                        nu[e] = quantize<S>(un.x);
+                        nu[e + 1] = quantize<S>(un.y);
+                        nv[e] = quantize<S>(vn.x);
+                        nv[e + 1] = quantize<S>(vn.y);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < N; ++e) {
+                        const int col = cl + e;
+                        const T c = P1[l - 1][e];
+                        T w = (e == 0) ? wsh : P1[l - 1][e - 1];
+                        T ea = (e == N - 1) ? esh : P1[l - 1][e + 1];
+                        if (col <= 0) w = c;
+                        if (col >= W - 1) ea = c;
+                        const T n = top ? c : P2[l - 1][e];
+                        const T s = bottom ? c : P0[l - 1][e];
+                        T un, vn;
+                        cell_update<MODE>(c, w, ea, n, s, Q1[l - 1][e], ph[e], m, un, vn);
+                        nu[e] = quantize<S>(un);
+                        nv[e] = quantize<S>(vn);
+                    }
                 }
             }
             if (l < K) {

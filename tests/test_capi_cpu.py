@@ -114,3 +114,13 @@ def test_create_ext_validates_before_touching_the_device(librdc):
         with pytest.raises(librdc.RdcError) as e:
             librdc.rdc_create_ext(16, 4, p, c["u"], c["v"], c["phi"], c["pitch"])
         assert e.value.status == librdc.RDC_EINVAL
+
+
+def test_check_division_validates_before_touching_the_device(librdc):
+    """Bad q values and a NULL report are refused before any device call."""
+    import ctypes
+    L = librdc.lib()
+    rep = librdc.rdc_division_report()
+    for q in (0.0, -0.5, float("nan"), float("inf")):
+        assert L.rdc_check_division(q, 0, 0, ctypes.byref(rep)) == librdc.RDC_EINVAL
+    assert L.rdc_check_division(0.002, 0, 0, None) == librdc.RDC_EINVAL
