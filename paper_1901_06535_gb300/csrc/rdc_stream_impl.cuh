@@ -74,13 +74,16 @@ struct StreamGeom {
 // launch (k_stepk_stream) and a work list over many grids (k_stream_batch).
 //
 // The row loop's body is straight-line code: every level computes its row
-// even when that row lies outside the grid (the phi load is clamped to a
-// real row), and the mirror borders are applied by selects.  Rows outside
-// the grid hold garbage that no valid cell ever reads: the select at rows
-// 0 and H-1 (and columns 0 and W-1) replaces the out-of-range neighbour by
-// the cell itself.  Straight-line code lets the compiler interleave the
+// even when that row lies outside the grid, and the mirror borders are
+// applied by selects.  Rows outside the grid hold garbage that no valid cell
+// ever reads: the select at rows 0 and H-1 (and columns 0 and W-1) replaces
+// the out-of-range neighbour by the cell itself.  phi of row t is loaded
+// with row t's u and v and handed down the levels in a K-deep register queue
+// (level l at iteration t needs row t - l), so each row's phi is read once
+// and one iteration before its first use; reloading it at every level made
+// load latency the main stall.  Straight-line code lets the compiler interleave the
 // levels' arithmetic; warp-uniform branches there measured slower.  For
-// K >= 5 the row loop is unrolled three times, which turns the three-row
+// K >= 4 the row loop is unrolled three times, which turns the three-row
 // register rotation into renaming.
 template <typename S, int MODE, int K, int N>
 __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
@@ -99,21 +102,25 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     const int t0 = max(y0 - K, 0);
     const int t_end = y1 - 1 + K;
     T P0[K][N], P1[K][N], P2[K][N], Q0[K][N], Q1[K][N];
+    T F[K][N];  // F[j]: phi of row t - 1 - j, loaded with that row's u and v
 #pragma unroll
     for (int l = 0; l < K; ++l)
 #pragma unroll
-        for (int e = 0; e < N; ++e) P0[l][e] = P1[l][e] = P2[l][e] = Q0[l][e] = Q1[l][e] = T(0);
-    constexpr int UNROLL = (K >= 5) ? 3 : 1;
+        for (int e = 0; e < N; ++e)
+            P0[l][e] = P1[l][e] = P2[l][e] = Q0[l][e] = Q1[l][e] = F[l][e] = T(0);
+    constexpr int UNROLL = (K >= 4) ? 3 : 1;
 #pragma unroll UNROLL
     for (int t = t0; t <= t_end; ++t) {
+        T nphi[N];
         {
             T nu[N], nv[N];
 #pragma unroll
-            for (int e = 0; e < N; ++e) nu[e] = nv[e] = T(0);
+            for (int e = 0; e < N; ++e) nu[e] = nv[e] = nphi[e] = T(0);
             if (t < H && in_grid) {
                 const int64_t o = (int64_t)t * pitch + cl;
                 VecN<S, N>::load(u + o, nu);
                 VecN<S, N>::load(v + o, nv);
+                VecN<typename Traits<S>::PhiT, N>::load(phi + o, nphi);
             }
 #pragma unroll
             for (int e = 0; e < N; ++e) {
@@ -129,14 +136,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
             const T wsh = __shfl_up_sync(0xffffffffu, P1[l - 1][N - 1], 1);
             const T esh = __shfl_down_sync(0xffffffffu, P1[l - 1][0], 1);
             {
-                T ph[N];
-                const int rc = min(max(r, 0), H - 1);   // rows outside the grid compute garbage
-                if (in_grid) {
-                    VecN<typename Traits<S>::PhiT, N>::load(phi + (int64_t)rc * pitch + cl, ph);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < N; ++e) ph[e] = T(0);
-                }
+                const T (&ph)[N] = F[l - 1];
                 const bool top = (r == 0), bottom = (r == H - 1);
                 if constexpr (sizeof(T) == 4 && N % 2 == 0) {
                     // FP32 compute: neighbouring cells in pairs (cell_update2).
@@ -201,6 +201,12 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                 }
             }
         }
+#pragma unroll
+        for (int j = K - 1; j > 0; --j)
+#pragma unroll
+            for (int e = 0; e < N; ++e) F[j][e] = F[j - 1][e];
+#pragma unroll
+        for (int e = 0; e < N; ++e) F[0][e] = nphi[e];
     }
 }
 
@@ -253,12 +259,14 @@ k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ item
     }
 }
 
-// Cells per lane.  FP32: 4 (16-byte vectors) while the K levels' registers
-// fit (K <= 4), 2 beyond (more halo columns, fewer registers).  16-bit
-// storage: 4 (8-byte u, v vectors; the FP32 phi vector is 16 bytes).  FP64: 1.
+// Cells per lane.  FP32 and 16-bit storage: 4 for K <= 3 (16-byte FP32
+// vectors; 8-byte 16-bit u, v vectors), 2 for K >= 4, where the K levels'
+// registers would otherwise cut the resident warps (measured: FP32 K = 4
+// 489 -> 670 G cell-updates/s at 8192^2, BF16 storage K = 6 474 -> 550).
+// FP64: 1.
 template <typename S, int K>
 struct StreamVec {
-    static constexpr int N = (sizeof(S) == 8) ? 1 : (sizeof(S) == 2 ? 4 : (K <= 4 ? 4 : 2));
+    static constexpr int N = (sizeof(S) == 8) ? 1 : (K <= 3 ? 4 : 2);
 };
 
 template <typename S, int K>
