@@ -324,6 +324,9 @@ def main():
         modes["bf16_tuned"] = _tuned(pkg, stream, "bf16")
         modes["f16_tuned"] = _tuned(pkg, stream, "f16")
         modes["f64"] = _mode_gcups(pkg, stream, "f64", 1, 100)
+        # stochastic rounding to the 16-bit storage (RDC_STOCH_ROUND = 4)
+        modes["bf16_stoch"] = _mode_gcups(pkg, stream, "bf16", 1, 1000, flags=4)
+        modes["bf16_stoch_tuned"] = _tuned(pkg, stream, "bf16", flags=4)
         extras = {"temporal_blocking_gcups": tb, "tuned_f32": tuned, "storage_modes_gcups": modes,
                   "batch_sweep": _batch_sweep(pkg, stream), "serving": _serving(pkg)}
     e2e = None if args.no_extras else _e2e(pkg, stream, h, disks, nE, args)
@@ -365,11 +368,12 @@ def main():
     return 0
 
 
-def _tuned(pkg, stream, mode, n=960):
+def _tuned(pkg, stream, mode, n=960, flags=0):
     """Autotuned shape on the 8192^2 grid and its GCUPS over n steps."""
     import torch
     prec = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}[mode]
-    h = pkg.rdc_create(W, H, pkg.rdc_params_default(precision=prec), None, stream.cuda_stream)
+    h = pkg.rdc_create(W, H, pkg.rdc_params_default(precision=prec, flags=flags), None,
+                       stream.cuda_stream)
     try:
         pkg.rdc_seed(h, W / 2, H / 2, 10.0, 0.8)
         shape, est = pkg.rdc_tune(h, 3)
@@ -387,10 +391,10 @@ def _tuned(pkg, stream, mode, n=960):
         pkg.rdc_destroy(h)
 
 
-def _mode_gcups(pkg, stream, mode, k, n, krows=None):
+def _mode_gcups(pkg, stream, mode, k, n, krows=None, flags=0):
     import torch
     prec = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}[mode]
-    p = pkg.rdc_params_default(precision=prec, k_block=k)
+    p = pkg.rdc_params_default(precision=prec, k_block=k, flags=flags)
     h = pkg.rdc_create(W, H, p, None, stream.cuda_stream)
     try:
         if krows is not None:

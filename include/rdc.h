@@ -77,9 +77,29 @@ extern "C" {
 #define RDC_DTYPE_BF16 2
 #define RDC_DTYPE_F16 3
 
-/* ---- flags (test modes; 0 = the full model) ------------------------------ */
-#define RDC_DIFFUSION_ONLY 1  /* drop the reaction term from u_t */
-#define RDC_REACTION_ONLY 2   /* drop Du lap(u) from u_t */
+/* ---- flags (0 = the full model, rounded to nearest) ---------------------- */
+#define RDC_DIFFUSION_ONLY 1  /* test mode: drop the reaction term from u_t */
+#define RDC_REACTION_ONLY 2   /* test mode: drop Du lap(u) from u_t */
+/*
+ * Stochastic rounding (16-bit storage only: RDC_F32_BF16STORE,
+ * RDC_F32_F16STORE).  Each new u', v' (an FP32 value x) is rounded to the
+ * storage type at random instead of to nearest: with lo = x rounded toward
+ * zero and hi the next storage value away from zero, the result is hi when
+ *     r16 < 2^16 (|x| - |lo|) / (|hi| - |lo|)
+ * and lo otherwise, r16 being 16 random bits (non-finite x, and FP16 beyond
+ * 65504, round to nearest).  The expected stored value is then x, so small
+ * per-step increments (dt (u - v) is often below half a BF16 spacing of v)
+ * survive on average instead of being lost every step.  r16 is the top half
+ * of a word of Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (column / 2, row, step index mod 2^32, step index / 2^32) and key
+ * (round_seed, 0): words 0 and 2 for the u and v of the even column of the
+ * pair, words 1 and 3 for the odd column.  The step index is the index of
+ * the state being written (steps since rdc_create or rdc_reset_rest).
+ * Results are deterministic and identical for every k_block, launch shape
+ * and batch; rdc_stoch_round_sample exposes the rounding.  Not available in
+ * rdc_step_noalloc.
+ */
+#define RDC_STOCH_ROUND 4
 
 typedef struct rdc_sim rdc_sim; /* opaque simulation handle */
 
@@ -97,14 +117,17 @@ typedef struct {
     double dt;         /* Euler timestep                       (Table 1: 0.001)  */
     double dx;         /* grid spacing                         (Table 1: 0.25)   */
     int32_t precision; /* RDC_F32 / RDC_F64 / RDC_F32_BF16STORE / RDC_F32_F16STORE */
-    int32_t flags;     /* RDC_DIFFUSION_ONLY | RDC_REACTION_ONLY (not both) */
+    int32_t flags;     /* RDC_DIFFUSION_ONLY | RDC_REACTION_ONLY (not both),
+                          | RDC_STOCH_ROUND */
     int32_t k_block;   /* Euler steps fused per launch (temporal blocking):
                           0 = library default (4 for FP32-compute grids of
                           >= 2^20 cells, else 1; see rdc_tune), 1 = one step
                           per launch,
                           2..8 = k steps per launch.  Results are bitwise
                           identical for every k. */
-    int32_t reserved;  /* must be 0 */
+    int32_t round_seed; /* key of the stochastic rounding stream (used as an
+                           unsigned 32-bit value); must be 0 without
+                           RDC_STOCH_ROUND */
 } rdc_params;
 
 /* Fills *out with Table 1 (eps, f, q, Du, dt, dx), RDC_F32, flags 0,
@@ -124,7 +147,9 @@ int rdc_params_default(rdc_params* out);
  *   out      : receives the handle; *out is NULL on failure.
  * Validation (RDC_EINVAL): W or H < 1; a non-finite parameter; eps, q, dt
  * or dx <= 0; Du < 0; f + q <= 1; Du dt / dx^2 > 1/4 (the explicit
- * diffusion limit); both test flags set; k_block outside 0..8; reserved != 0.
+ * diffusion limit); both test flags set; RDC_STOCH_ROUND with FP32 or FP64
+ * storage; an unknown flag; k_block outside 0..8; round_seed != 0 without
+ * RDC_STOCH_ROUND.
  * The device must be sm_103 (RDC_EUNSUPPORTED otherwise).
  */
 int rdc_create(rdc_grid g, const rdc_params* p, const float* phi_host,
@@ -542,6 +567,21 @@ typedef struct {
 } rdc_division_report;
 
 int rdc_check_division(double q, uint64_t n_random, uint64_t seed, rdc_division_report* out);
+
+/*
+ * The paper has no counterpart: exposes the stochastic rounding of
+ * RDC_STOCH_ROUND.  For i in 0..n-1, rounds the FP32 value x[i] to the
+ * storage type of `precision` (RDC_F32_BF16STORE or RDC_F32_F16STORE) as the
+ * step kernels round the new u (u_out[i]) and the new v (v_out[i]) of the
+ * cell in column col0 + i, row `row`, when they write the state with index
+ * `step` under key `seed`; the results are widened back to float.  Host
+ * arrays of n floats (copied).  Synchronous; allocates and frees device
+ * memory.  RDC_EINVAL: another precision, n < 0, col0 or row < 0, col0 + n
+ * beyond 2^31 - 1, or a NULL array with n > 0.
+ */
+int rdc_stoch_round_sample(int32_t precision, uint32_t seed, int64_t step, int32_t row,
+                           int32_t col0, int32_t n, const float* x, float* u_out,
+                           float* v_out);
 
 /* Human-readable name of a status code (static storage). */
 const char* rdc_status_str(int status);

@@ -22,6 +22,12 @@ Parity status of the functions (what pins each one is in ``tests/``):
   * arrival times in run     -- parity unpinned: the paper prints no wave
                                 speeds or arrival times; only the
                                 interpolation rule itself is checked.
+  * round_stoch              -- pinned (exact unbiasedness over all 2^16
+                                random values, both neighbours on the target
+                                grid, round-to-nearest cases)
+  * philox4x32_10            -- partly pinned: bijectivity in each counter
+                                word, avalanche and uniformity of the output
+                                bits; no published output values are used.
 """
 from __future__ import annotations
 
@@ -149,6 +155,16 @@ class Oracle:
         lib.orc_draw_line.argtypes = [ctypes.c_int32, ctypes.c_int32, dp] + [ctypes.c_double] * 6
         lib.orc_draw_line.restype = ctypes.c_int64
         lib.orc_max_threads.argtypes = []
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        lib.orc_philox4x32_10.restype = None
+        lib.orc_round_stoch.argtypes = [ctypes.c_float, ctypes.c_uint32, ctypes.c_int32]
+        lib.orc_round_stoch.restype = ctypes.c_float
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.orc_round_stoch_cells.argtypes = [ctypes.c_int64, fp, ctypes.c_uint32, ctypes.c_int64,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              fp, fp]
+        lib.orc_round_stoch_cells.restype = None
         lib.orc_max_threads.restype = ctypes.c_int32
         self.lib = lib
 
@@ -275,6 +291,36 @@ class Oracle:
 
     def max_threads(self) -> int:
         return int(self.lib.orc_max_threads())
+
+    # -- stochastic rounding to 16-bit storage ---------------------------------
+    def philox4x32_10(self, ctr, key):
+        """Four 32-bit output words of Philox4x32-10 for counter ctr[4], key[2]."""
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        c = np.ascontiguousarray(ctr, dtype=np.uint32)
+        k = np.ascontiguousarray(key, dtype=np.uint32)
+        out = np.empty(4, dtype=np.uint32)
+        self.lib.orc_philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p),
+                                   out.ctypes.data_as(u32p))
+        return out
+
+    def round_stoch(self, x: float, r16: int, fmt: str) -> float:
+        """x (a float32 value) rounded stochastically to "bf16" or "f16" with
+        the 16-bit random value r16; returned as a Python float."""
+        return float(self.lib.orc_round_stoch(float(np.float32(x)), int(r16),
+                                              0 if fmt == "bf16" else 1))
+
+    def round_stoch_cells(self, x, seed: int, step: int, row: int, col0: int, fmt: str):
+        """The rounding of the u and v of cells (col0 + i, row) writing state
+        `step` with key `seed`; float32 arrays (u, v)."""
+        fp = ctypes.POINTER(ctypes.c_float)
+        x = np.ascontiguousarray(x, dtype=np.float32).ravel()
+        u = np.empty_like(x)
+        v = np.empty_like(x)
+        self.lib.orc_round_stoch_cells(x.size, x.ctypes.data_as(fp), int(seed) & 0xFFFFFFFF,
+                                       int(step), int(row), int(col0),
+                                       0 if fmt == "bf16" else 1,
+                                       u.ctypes.data_as(fp), v.ctypes.data_as(fp))
+        return u, v
 
 
 def load(force_rebuild: bool = False) -> Oracle:

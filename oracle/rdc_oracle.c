@@ -422,3 +422,100 @@ int64_t orc_draw_line(int32_t W, int32_t H, double* phi, double x0, double y0,
     }
     return count;
 }
+
+/* ------------------------------------------------------------------------
+ * Stochastic rounding to 16-bit storage (the RDC_STOCH_ROUND variant of the
+ * storage conversion).  The paper stores nothing in reduced precision; this
+ * is the rounding rule of the variant, written from its definition:
+ *   lo = x rounded toward zero onto the target grid, hi = the next grid
+ *   value away from zero; result hi iff r16 < 2^16 (|x| - |lo|) / (|hi| -
+ *   |lo|), else lo; non-finite x, and FP16 at or beyond 65504, round to
+ *   nearest.
+ * The random words are Philox4x32-10 (J. K. Salmon, M. A. Moraes, R. O.
+ * Dror, D. E. Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+ * ------------------------------------------------------------------------ */
+
+/* Philox4x32 with 10 rounds.  One round: the products M0 * c0 and M1 * c2
+ * (64-bit); the new counter is (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2),
+ * hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); then the key advances by the Weyl
+ * increments.  M0 = 0xD2511F53, M1 = 0xCD9E8D57, increments 0x9E3779B9 and
+ * 0xBB67AE85 (the constants of the paper's Philox4x32). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+        const uint32_t n1 = (uint32_t)p1;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        const uint32_t n3 = (uint32_t)p0;
+        c[0] = n0;
+        c[1] = n1;
+        c[2] = n2;
+        c[3] = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    memcpy(out, c, sizeof c);
+}
+
+/* Grid spacing of the target format at |x| (x finite, nonzero or zero):
+ * mant = stored significand bits, emin = smallest normal exponent. */
+static double orc_spacing(double ax, int mant, int emin)
+{
+    int e = emin;
+    if (ax >= ldexp(1.0, emin)) {
+        (void)frexp(ax, &e); /* ax = m 2^e, m in [0.5, 1) */
+        e -= 1;              /* ax in [2^e, 2^(e+1)) */
+    }
+    return ldexp(1.0, e - mant);
+}
+
+/* fmt 0: BF16 (8 significant bits, exponent range of FP32);
+ * fmt 1: FP16 (11 significant bits, smallest normal 2^-14, largest 65504). */
+float orc_round_stoch(float x, uint32_t r16, int32_t fmt)
+{
+    const int mant = fmt == 0 ? 7 : 10;
+    const int emin = fmt == 0 ? -126 : -14;
+    const double xd = (double)x;
+    if (isnan(xd)) return x;
+    const double ax = fabs(xd);
+    const double sgn = signbit(xd) ? -1.0 : 1.0;
+    if (fmt == 1 && !(ax < 65504.0)) {
+        if (isinf(ax)) return x;
+        /* RN: 65504 below the midpoint 65520, infinity from it (the tie goes
+         * to the even significand, which is the next binade) */
+        return (float)(sgn * (ax < 65520.0 ? 65504.0 : INFINITY));
+    }
+    if (isinf(ax)) return x;
+    const double sp = orc_spacing(ax, mant, emin);
+    const double lo = floor(ax / sp) * sp;
+    if (lo == ax) return x;
+    const double frac = (ax - lo) / sp; /* exact: sp is a power of two */
+    double mag = ((double)r16 < ldexp(frac, 16)) ? lo + sp : lo;
+    if (fmt == 0 && mag >= ldexp(1.0, 128)) mag = INFINITY;
+    return (float)(sgn * mag);
+}
+
+/* The rounding of the u (out_u) and the v (out_v) of cells (col0 + i, row)
+ * for the state with index `step`, key seed: counter (col / 2, row, step mod
+ * 2^32, step / 2^32), key (seed, 0); words 0, 2 for an even column, 1, 3 for
+ * an odd one; each word's top 16 bits. */
+void orc_round_stoch_cells(int64_t n, const float* x, uint32_t seed, int64_t step, int32_t row,
+                           int32_t col0, int32_t fmt, float* out_u, float* out_v)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t col = (int64_t)col0 + i;
+        const uint64_t s = (uint64_t)step;
+        const uint32_t ctr[4] = {(uint32_t)(col / 2), (uint32_t)row, (uint32_t)s,
+                                 (uint32_t)(s >> 32)};
+        const uint32_t key[2] = {seed, 0u};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        const int odd = (int)(col % 2);
+        out_u[i] = orc_round_stoch(x[i], w[odd] >> 16, fmt);
+        out_v[i] = orc_round_stoch(x[i], w[2 + odd] >> 16, fmt);
+    }
+}

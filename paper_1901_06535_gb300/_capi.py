@@ -39,6 +39,7 @@ RDC_DTYPE_F16 = 3
 
 RDC_DIFFUSION_ONLY = 1
 RDC_REACTION_ONLY = 2
+RDC_STOCH_ROUND = 4
 
 PRECISION_NAMES = {"f32": RDC_F32, "f64": RDC_F64, "bf16": RDC_F32_BF16STORE,
                    "f16": RDC_F32_F16STORE}
@@ -53,7 +54,7 @@ class rdc_params(ctypes.Structure):
                 ("q", ctypes.c_double), ("Du", ctypes.c_double),
                 ("dt", ctypes.c_double), ("dx", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("k_block", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("k_block", ctypes.c_int32), ("round_seed", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -166,6 +167,9 @@ _SIGS = {
     "rdc_timelapse_record": (ctypes.c_int, [_P, ctypes.c_int32]),
     "rdc_check_division": (ctypes.c_int, [ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.POINTER(rdc_division_report)]),
+    "rdc_stoch_round_sample": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              _P, _P, _P]),
     "rdc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "rdc_last_error": (ctypes.c_char_p, []),
 }
@@ -261,9 +265,14 @@ def rdc_last_error() -> str:
 def rdc_params_default(**overrides) -> rdc_params:
     p = rdc_params()
     _chk(lib().rdc_params_default(ctypes.byref(p)), "rdc_params_default")
+    fields = {f for f, _ in p._fields_}
     for k, v in overrides.items():
+        if k not in fields:
+            raise TypeError(f"rdc_params has no field {k!r}")
         if k == "precision" and isinstance(v, str):
             v = PRECISION_NAMES[v]
+        if k == "round_seed":
+            v = ctypes.c_int32(int(v) & 0xFFFFFFFF).value   # an unsigned 32-bit key
         setattr(p, k, v)
     return p
 
@@ -396,6 +405,22 @@ def rdc_check_division(q: float = 0.002, n_random: int = 1 << 26, seed: int = 1)
     _chk(lib().rdc_check_division(float(q), int(n_random), int(seed), ctypes.byref(rep)),
          "rdc_check_division")
     return rep.as_dict()
+
+
+def rdc_stoch_round_sample(precision, seed: int, step: int, row: int, col0: int, x):
+    """Rounds each float32 x[i] as the step kernels round the new u and v of
+    cell (col0 + i, row) writing state `step` under RDC_STOCH_ROUND with key
+    `seed`; returns (u, v) float32 arrays (widened back from 16 bits)."""
+    if isinstance(precision, str):
+        precision = PRECISION_NAMES[precision]
+    x = np.ascontiguousarray(x, dtype=np.float32).ravel()
+    u = np.empty_like(x)
+    v = np.empty_like(x)
+    _chk(lib().rdc_stoch_round_sample(int(precision), int(seed) & 0xFFFFFFFF, int(step),
+                                      int(row), int(col0), int(x.size),
+                                      x.ctypes.data, u.ctypes.data, v.ctypes.data),
+         "rdc_stoch_round_sample")
+    return u, v
 
 
 def rdc_step_noalloc(width: int, height: int, params: rdc_params, u_in: int, v_in: int,

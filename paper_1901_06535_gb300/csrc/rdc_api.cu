@@ -38,10 +38,10 @@ cudaError_t launch_stream_f64(const Planes&, const ModelD&, int, int, cudaStream
 cudaError_t launch_stream_bf16(const Planes&, const ModelD&, int, int, cudaStream_t);
 cudaError_t launch_stream_f16(const Planes&, const ModelD&, int, int, cudaStream_t);
 #define RDC_DECL_BATCH(n)                                                                   \
-    cudaError_t launch_batch_step1_##n(const GridDesc*, const Item*, int, int, int,         \
-                                       cudaStream_t);                                       \
-    cudaError_t launch_batch_stream_##n(const GridDesc*, const Item*, int, int, int, int,   \
-                                        cudaStream_t);                                      \
+    cudaError_t launch_batch_step1_##n(const GridDesc*, const Item*, int, int, long long,   \
+                                       int, int, cudaStream_t);                             \
+    cudaError_t launch_batch_stream_##n(const GridDesc*, const Item*, int, int, int,        \
+                                        long long, int, int, cudaStream_t);                 \
     int batch_stream_outc_##n(int);
 RDC_DECL_BATCH(f32)
 RDC_DECL_BATCH(f64)
@@ -50,25 +50,26 @@ RDC_DECL_BATCH(f16)
 #undef RDC_DECL_BATCH
 
 cudaError_t launch_batch_step1(int prec, const GridDesc* d, const Item* items, int nitems,
-                               int j, int ctas, cudaStream_t st)
+                               int j, long long sbase, int sr, int ctas, cudaStream_t st)
 {
     switch (prec) {
-        case P_F32: return launch_batch_step1_f32(d, items, nitems, j, ctas, st);
-        case P_F64: return launch_batch_step1_f64(d, items, nitems, j, ctas, st);
-        case P_BF16: return launch_batch_step1_bf16(d, items, nitems, j, ctas, st);
-        case P_F16: return launch_batch_step1_f16(d, items, nitems, j, ctas, st);
+        case P_F32: return launch_batch_step1_f32(d, items, nitems, j, sbase, sr, ctas, st);
+        case P_F64: return launch_batch_step1_f64(d, items, nitems, j, sbase, sr, ctas, st);
+        case P_BF16: return launch_batch_step1_bf16(d, items, nitems, j, sbase, sr, ctas, st);
+        case P_F16: return launch_batch_step1_f16(d, items, nitems, j, sbase, sr, ctas, st);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_batch_stream(int prec, const GridDesc* d, const Item* items, int nitems,
-                                int k, int j, int ctas, cudaStream_t st)
+                                int k, int j, long long sbase, int sr, int ctas,
+                                cudaStream_t st)
 {
     switch (prec) {
-        case P_F32: return launch_batch_stream_f32(d, items, nitems, k, j, ctas, st);
-        case P_F64: return launch_batch_stream_f64(d, items, nitems, k, j, ctas, st);
-        case P_BF16: return launch_batch_stream_bf16(d, items, nitems, k, j, ctas, st);
-        case P_F16: return launch_batch_stream_f16(d, items, nitems, k, j, ctas, st);
+        case P_F32: return launch_batch_stream_f32(d, items, nitems, k, j, sbase, sr, ctas, st);
+        case P_F64: return launch_batch_stream_f64(d, items, nitems, k, j, sbase, sr, ctas, st);
+        case P_BF16: return launch_batch_stream_bf16(d, items, nitems, k, j, sbase, sr, ctas, st);
+        case P_F16: return launch_batch_stream_f16(d, items, nitems, k, j, sbase, sr, ctas, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -202,6 +203,8 @@ static ModelD model_of(const rdc_params& p)
     m.Du = p.Du;
     m.dt = p.dt;
     m.inv_dx2 = 1.0 / (p.dx * p.dx);
+    m.sr = (p.flags & RDC_STOCH_ROUND) ? 1 : 0;
+    m.seed = (unsigned)p.round_seed;
     return m;
 }
 
@@ -217,9 +220,13 @@ bool host_params_valid(const rdc_params* p)
     if (!(p->f + p->q > 1.0)) return false;
     if (p->Du * p->dt / (p->dx * p->dx) > 0.25) return false;
     if (p->precision < 0 || p->precision > 3) return false;
-    if (p->flags < 0 || p->flags > 2) return false;
+    if (p->flags & ~(RDC_DIFFUSION_ONLY | RDC_REACTION_ONLY | RDC_STOCH_ROUND)) return false;
+    if ((p->flags & RDC_DIFFUSION_ONLY) && (p->flags & RDC_REACTION_ONLY)) return false;
+    const bool sr = (p->flags & RDC_STOCH_ROUND) != 0;
+    if (sr && p->precision != RDC_F32_BF16STORE && p->precision != RDC_F32_F16STORE)
+        return false;
+    if (!sr && p->round_seed != 0) return false;
     if (p->k_block < 0 || p->k_block > 8) return false;
-    if (p->reserved != 0) return false;
     return true;
 }
 
@@ -376,7 +383,7 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
     s->H = g.height;
     s->p = *p;
     s->prec = prec;
-    s->mode = p->flags;
+    s->mode = p->flags & (RDC_DIFFUSION_ONLY | RDC_REACTION_ONLY);
     s->phi_max = phi_max;
     if (stream) {
         s->stream = (cudaStream_t)stream;
@@ -465,7 +472,7 @@ int rdc_params_default(rdc_params* out)
     out->precision = RDC_F32;
     out->flags = 0;
     out->k_block = 0;
-    out->reserved = 0;
+    out->round_seed = 0;
     return RDC_OK;
 }
 
@@ -551,7 +558,7 @@ int rdc_set_state(rdc_sim* s, const void* u_host, const void* v_host, int32_t dt
 int rdc_step(rdc_sim* s, int64_t n)
 {
     if (!s || n < 0) return RDC_EINVAL;
-    const ModelD m = model_of(s->p);
+    ModelD m = model_of(s->p);
     int64_t left = n;
     const int k = s->shapek.k;
     while (left > 0) {
@@ -559,6 +566,7 @@ int rdc_step(rdc_sim* s, int64_t n)
                  s->W, s->H, s->pitch};
         cudaError_t e;
         int done;
+        m.step0 = s->steps_done;  // index of the state this launch reads
         if (k > 1 && left >= k) {
             e = launch_kblock(s->prec, s->mode, g, m, s->shapek, s->stream);
             done = k;

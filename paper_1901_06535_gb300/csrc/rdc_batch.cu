@@ -46,6 +46,7 @@ struct rdc_batch {
     int n = 0;                       // slots (live or free)
     int prec = 0;
     int k_block = 0;
+    int sr = 0;                      // RDC_STOCH_ROUND on every grid
     std::vector<rdc_grid> grids;
     std::vector<rdc_params> params;
     std::vector<GridDesc> desc;      // host copy; par kept current
@@ -149,13 +150,14 @@ int enqueue_sequence(rdc_batch* b, int64_t n, int64_t* launches)
     int64_t j = 0, left = n;
     while (left > 0) {
         cudaError_t e;
+        const long long sbase = (long long)(n - left);  // steps of this call already enqueued
         if (k > 1 && left >= k) {
-            e = launch_batch_stream(b->prec, b->d_desc, sk->dev, sk->n, k, (int)(j & 1),
-                                    persistent_ctas(sk->n), b->stream);
+            e = launch_batch_stream(b->prec, b->d_desc, sk->dev, sk->n, k, (int)(j & 1), sbase,
+                                    b->sr, persistent_ctas(sk->n), b->stream);
             left -= k;
         } else {
-            e = launch_batch_step1(b->prec, b->d_desc, s1->dev, s1->n, (int)(j & 1),
-                                   persistent_ctas(s1->n), b->stream);
+            e = launch_batch_step1(b->prec, b->d_desc, s1->dev, s1->n, (int)(j & 1), sbase,
+                                   b->sr, persistent_ctas(s1->n), b->stream);
             left -= 1;
         }
         if (e != cudaSuccess) return host_cuda_fail(e, "batched step kernel");
@@ -230,6 +232,8 @@ int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const flo
     d.dt = p.dt;
     d.inv_dx2 = 1.0 / (p.dx * p.dx);
     d.par = 0;
+    d.seed = (unsigned)p.round_seed;
+    d.steps = 0;
     if (e == cudaSuccess) {
         if (phi_host) {
             const size_t bytes = (size_t)grid.width * grid.height * sizeof(float);
@@ -262,7 +266,7 @@ int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const flo
 bool grid_ok(const rdc_batch* b, rdc_grid grid, const rdc_params* p, const float* phi_host)
 {
     if (grid.width < 1 || grid.height < 1 || !host_params_valid(p)) return false;
-    if (p->precision != b->prec || p->flags != 0) return false;
+    if (p->precision != b->prec || p->flags != (b->sr ? RDC_STOCH_ROUND : 0)) return false;
     double mx = 0.0;
     if (phi_host)
         return host_scan_phi(phi_host, 0, (int64_t)grid.width * grid.height, p, &mx);
@@ -296,13 +300,15 @@ int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
     if (!out) return RDC_EINVAL;
     *out = nullptr;
     if (n < 0 || !params || (n > 0 && !grids)) return RDC_EINVAL;
-    if (!host_params_valid(&params[0]) || params[0].flags != 0) return RDC_EINVAL;
+    if (!host_params_valid(&params[0]) || (params[0].flags & ~RDC_STOCH_ROUND) != 0)
+        return RDC_EINVAL;
     int rc = host_check_device();
     if (rc) return rc;
     rdc_batch* b = new (std::nothrow) rdc_batch();
     if (!b) return RDC_ENOMEM;
     b->prec = params[0].precision;
     b->k_block = params[0].k_block;
+    b->sr = (params[0].flags & RDC_STOCH_ROUND) ? 1 : 0;
     b->cfg.k = b->k_block == 0 ? 1 : b->k_block;
     for (int g = 0; g < n; ++g) {
         if (params[g].k_block != b->k_block ||
@@ -478,6 +484,7 @@ int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n)
     }
     for (int g : subset) {
         b->desc[g].par = (int)((b->desc[g].par + L) & 1);
+        b->desc[g].steps += n;
         b->cells_stepped += (double)b->grids[g].width * b->grids[g].height * (double)n;
     }
     b->launches += L;
@@ -614,9 +621,9 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
         // Every timed launch reads the current buffers (j = 0) and writes the
         // spare ones, so tuning never advances the state.
         auto launch = [&]() {
-            return c.k > 1 ? launch_batch_stream(b->prec, b->d_desc, L->dev, L->n, c.k, 0,
-                                                 persistent_ctas(L->n), b->stream)
-                           : launch_batch_step1(b->prec, b->d_desc, L->dev, L->n, 0,
+            return c.k > 1 ? launch_batch_stream(b->prec, b->d_desc, L->dev, L->n, c.k, 0, 0,
+                                                 b->sr, persistent_ctas(L->n), b->stream)
+                           : launch_batch_step1(b->prec, b->d_desc, L->dev, L->n, 0, 0, b->sr,
                                                 persistent_ctas(L->n), b->stream);
         };
         cudaError_t e = launch();  // warm-up

@@ -1,3 +1,7 @@
+// Diagnostics of the step kernels' arithmetic: rdc_check_division checks
+// the FP32 division exhaustively, rdc_stoch_round_sample exposes the
+// stochastic rounding of RDC_STOCH_ROUND.
+//
 // rdc_check_division: exhaustive device check of the FP32 division that
 // every FP32 step kernel uses for the ratio (u - q)/(u + q) of Eq. 1.
 //
@@ -129,10 +133,54 @@ __global__ void k_check_random(uint64_t n_pairs, uint64_t seed, Counts* out)
     flush(out, 2, n, bad, first);
 }
 
+// The rounding of the step kernels for the u and the v of cells
+// (col0 + i, row) writing state `step`.
+template <typename S>
+__global__ void k_sr_sample(const float* __restrict__ x, int n, unsigned seed, long long step,
+                            int row, int col0, float* __restrict__ uo, float* __restrict__ vo)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int col = col0 + i;
+    const Philox4 rb = sr_pair_bits(seed, col >> 1, row, step);
+    uo[i] = quantize_sr<S>(x[i], (col & 1) ? rb.y : rb.x);
+    vo[i] = quantize_sr<S>(x[i], (col & 1) ? rb.w : rb.z);
+}
+
 }  // namespace
 }  // namespace rdc
 
 using namespace rdc;
+
+extern "C" int rdc_stoch_round_sample(int32_t precision, uint32_t seed, int64_t step,
+                                      int32_t row, int32_t col0, int32_t n, const float* x,
+                                      float* u_out, float* v_out)
+{
+    if ((precision != RDC_F32_BF16STORE && precision != RDC_F32_F16STORE) || n < 0 ||
+        col0 < 0 || row < 0 || (int64_t)col0 + n > 2147483647LL ||
+        (n > 0 && (!x || !u_out || !v_out)))
+        return RDC_EINVAL;
+    if (n == 0) return RDC_OK;
+    int rc = host_check_device();
+    if (rc) return rc;
+    float* d = nullptr;
+    const size_t bytes = (size_t)n * sizeof(float);
+    cudaError_t e = cudaMalloc((void**)&d, 3 * bytes);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(rounding sample)");
+    do {
+        if ((e = cudaMemcpy(d, x, bytes, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+        const int bs = 256, gs = (n + bs - 1) / bs;
+        if (precision == RDC_F32_BF16STORE)
+            k_sr_sample<__nv_bfloat16><<<gs, bs>>>(d, n, seed, step, row, col0, d + n, d + 2 * (size_t)n);
+        else
+            k_sr_sample<__half><<<gs, bs>>>(d, n, seed, step, row, col0, d + n, d + 2 * (size_t)n);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = cudaMemcpy(u_out, d + n, bytes, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+        e = cudaMemcpy(v_out, d + 2 * (size_t)n, bytes, cudaMemcpyDeviceToHost);
+    } while (false);
+    cudaFree(d);
+    return e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "rounding sample");
+}
 
 extern "C" int rdc_check_division(double q, uint64_t n_random, uint64_t seed,
                                   rdc_division_report* out)

@@ -12,10 +12,14 @@ namespace rdc {
 // to its compute precision.
 struct ModelD {
     double eps, f, q, Du, dt, inv_dx2;
+    int sr = 0;           // 1: stochastic rounding to the 16-bit storage type
+    unsigned seed = 0;    // key of the rounding stream
+    long long step0 = 0;  // index of the state a launch reads; level l writes step0 + l
 };
 
-// Which terms of u_t a step evaluates (match the RDC_*_ONLY flags).
-enum { MODE_FULL = 0, MODE_DIFFUSION = 1, MODE_REACTION = 2 };
+// Which terms of u_t a step evaluates (match the RDC_*_ONLY flags), plus
+// MODE_SR for stochastic rounding to the storage type.
+enum { MODE_FULL = 0, MODE_DIFFUSION = 1, MODE_REACTION = 2, MODE_SR = 4 };
 
 // Storage codes (match RDC_F32 ... RDC_F32_F16STORE).
 enum Prec { P_F32 = 0, P_F64 = 1, P_BF16 = 2, P_F16 = 3 };
@@ -64,7 +68,10 @@ struct GridDesc {
     long long pitch;  // elements, all planes
     double eps, f, q, Du, dt, inv_dx2;
     int par;
-    int active;  // 0: this call leaves the grid alone (its items are skipped)
+    int active;       // 0: this call leaves the grid alone (its items are skipped)
+    unsigned seed;    // stochastic rounding key (RDC_STOCH_ROUND)
+    int pad_;
+    long long steps;  // Euler steps taken by the grid before the current call
 };
 
 // A work item of a batched launch: one warp's strip of one grid.
@@ -84,10 +91,13 @@ cudaError_t launch_stream(int prec, const Planes& g, const ModelD& m, int k, int
                           cudaStream_t st);
 // Batched launches over a device item list (persistent: `ctas` CTAs of 128
 // threads, each warp looping over items); launch index j selects buffers.
+// sbase: Euler steps of the call before this launch (the rounding stream's
+// step index is the grid's steps + sbase + level); sr: stochastic rounding.
 cudaError_t launch_batch_step1(int prec, const GridDesc* d, const Item* items, int nitems,
-                               int j, int ctas, cudaStream_t st);
+                               int j, long long sbase, int sr, int ctas, cudaStream_t st);
 cudaError_t launch_batch_stream(int prec, const GridDesc* d, const Item* items, int nitems,
-                                int k, int j, int ctas, cudaStream_t st);
+                                int k, int j, long long sbase, int sr, int ctas,
+                                cudaStream_t st);
 // Columns a warp covers (single step) / writes (streamed, k steps).
 int batch_step1_cols(int prec);
 int batch_stream_outc(int prec, int k);

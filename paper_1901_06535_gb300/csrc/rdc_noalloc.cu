@@ -69,7 +69,7 @@ bool params_ok(const rdc_params* p)
         return false;
     if (p->Du * p->dt / (p->dx * p->dx) > 0.25) return false;
     if (p->precision < 0 || p->precision > 3 || p->flags < 0 || p->flags > 2) return false;
-    if (p->k_block < 0 || p->k_block > 8 || p->reserved != 0) return false;
+    if (p->k_block < 0 || p->k_block > 8 || p->round_seed != 0) return false;
     return true;
 }
 

@@ -18,10 +18,43 @@
 //            launch of k_stepk give the same bits.
 #pragma once
 
+#include <type_traits>
+
 #include "rdc_device.cuh"
 #include "rdc_internal.h"
 
 namespace rdc {
+
+// Calls f(std::integral_constant<int, MODE>) for the step kernel's template
+// mode: the physics mode, plus MODE_SR with stochastic rounding, which only
+// the 16-bit storage types instantiate.
+template <typename S, int M, typename F>
+cudaError_t call_mode(F&& f)
+{
+    if constexpr ((M & MODE_SR) != 0 && sizeof(S) != 2) return cudaErrorInvalidValue;
+    else return f(std::integral_constant<int, M>{});
+}
+
+// The full model only (streamed and batched kernels).
+template <typename S, typename F>
+cudaError_t dispatch_full(bool sr, F&& f)
+{
+    return sr ? call_mode<S, MODE_FULL | MODE_SR>(f) : call_mode<S, MODE_FULL>(f);
+}
+
+template <typename S, typename F>
+cudaError_t dispatch_mode(int mode, bool sr, F&& f)
+{
+    switch (mode) {
+        case MODE_FULL:
+            return sr ? call_mode<S, MODE_FULL | MODE_SR>(f) : call_mode<S, MODE_FULL>(f);
+        case MODE_DIFFUSION:
+            return sr ? call_mode<S, MODE_DIFFUSION | MODE_SR>(f) : call_mode<S, MODE_DIFFUSION>(f);
+        case MODE_REACTION:
+            return sr ? call_mode<S, MODE_REACTION | MODE_SR>(f) : call_mode<S, MODE_REACTION>(f);
+    }
+    return cudaErrorInvalidValue;
+}
 
 // One warp's share of a single Euler step: 32 vectors of VEC cells starting
 // at column wcol0, rows [row0, row1).  Warps are independent (no shared
@@ -94,6 +127,17 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
                     cell_update<MODE>(uc[e], w, ea, un[e], us[e], vv[e], ph[e], m, ou[e], ov[e]);
                 }
             }
+            if constexpr ((MODE & MODE_SR) != 0) {
+                // stochastic rounding of the new state (index step0 + 1)
+#pragma unroll
+                for (int e = 0; e < VEC; e += 2) {
+                    const Philox4 rb = sr_pair_bits(m.seed, (col0 + e) >> 1, r, m.step0 + 1);
+                    ou[e] = quantize_sr<S>(ou[e], rb.x);
+                    ou[e + 1] = quantize_sr<S>(ou[e + 1], rb.y);
+                    ov[e] = quantize_sr<S>(ov[e], rb.z);
+                    ov[e + 1] = quantize_sr<S>(ov[e + 1], rb.w);
+                }
+            }
             if (col0 + VEC <= W) {
                 Vec<S>::store(u1 + ro + col0, ou);
                 Vec<S>::store(v1 + ro + col0, ov);
@@ -143,15 +187,17 @@ __device__ __forceinline__ Model<T> model_of(const GridDesc& d)
     m.inv_dx2 = (T)d.inv_dx2;
     m.dt_Dux = (T)(__dmul_rn(__dmul_rn(d.dt, d.Du), d.inv_dx2));
     m.dt_eps = (T)(__ddiv_rn(d.dt, d.eps));
+    m.seed = d.seed;
+    m.step0 = d.steps;
     return m;
 }
 
 // Persistent single step over a batch of grids: every warp takes items
 // w, w + (all warps), ...; each item is one warp's strip of one grid.
-template <typename S>
+template <typename S, int MODE>
 __global__ void __launch_bounds__(128)
 k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
-              int j)
+              int j, long long sbase)
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
@@ -162,20 +208,25 @@ k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items
         const GridDesc& d = descs[item.g];
         if (!d.active) continue;
         const int par = (d.par + j) & 1;
-        step1_warp<S, MODE_FULL>(static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
-                                 static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
-                                 static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0,
-                                 item.y0, item.y1, model_of<T>(d));
+        Model<T> m = model_of<T>(d);
+        m.step0 += sbase;
+        step1_warp<S, MODE>(static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
+                            static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
+                            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0,
+                            item.y0, item.y1, m);
     }
 }
 
 template <typename S>
 cudaError_t launch_batch_step1_t(const GridDesc* d, const Item* items, int nitems, int j,
-                                 int ctas, cudaStream_t st)
+                                 long long sbase, int sr, int ctas, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
     if (ctas < 1) return cudaErrorInvalidValue;
-    return launch_pdl(k_step1_batch<S>, dim3(ctas), dim3(128), 0, st, d, items, nitems, j);
+    return dispatch_full<S>(sr != 0, [&](auto mc) {
+        return launch_pdl(k_step1_batch<S, decltype(mc)::value>, dim3(ctas), dim3(128), 0, st, d,
+                          items, nitems, j, sbase);
+    });
 }
 
 // Shared-memory layout of k_stepk: four planes of (tx+2k) x (ty+2k) compute
@@ -236,8 +287,14 @@ k_stepk(const S* __restrict__ u, const S* __restrict__ v,
                 const T so_v = cur[i + so];
                 T un, vn;
                 cell_update<MODE>(c, w, e, n, so_v, vs[i], ps[i], m, un, vn);
-                nxt[i] = quantize<S>(un);
-                vs[i] = quantize<S>(vn);
+                if constexpr ((MODE & MODE_SR) != 0) {
+                    const Philox4 rb = sr_pair_bits(m.seed, gx >> 1, gy, m.step0 + s);
+                    nxt[i] = quantize_sr<S>(un, (gx & 1) ? rb.y : rb.x);
+                    vs[i] = quantize_sr<S>(vn, (gx & 1) ? rb.w : rb.z);
+                } else {
+                    nxt[i] = quantize<S>(un);
+                    vs[i] = quantize<S>(vn);
+                }
             }
         }
         __syncthreads();
@@ -272,6 +329,8 @@ Model<typename Traits<S>::T> make_model(const ModelD& d)
     m.inv_dx2 = (T)d.inv_dx2;
     m.dt_Dux = (T)((d.dt * d.Du) * d.inv_dx2);
     m.dt_eps = (T)(d.dt / d.eps);
+    m.seed = d.seed;
+    m.step0 = d.step0;
     return m;
 }
 
@@ -294,18 +353,10 @@ cudaError_t launch_step1_t(int mode, const Planes& g, const ModelD& md, Shape1 s
     S* u1 = static_cast<S*>(g.u1);
     S* v1 = static_cast<S*>(g.v1);
     const dim3 block(sh.bx);
-    switch (mode) {
-        case MODE_FULL:
-            return launch_pdl(k_step1<S, MODE_FULL>, grid, block, 0, st, u, v, phi, u1, v1, g.W,
-                              g.H, g.pitch, rows, m);
-        case MODE_DIFFUSION:
-            return launch_pdl(k_step1<S, MODE_DIFFUSION>, grid, block, 0, st, u, v, phi, u1, v1,
-                              g.W, g.H, g.pitch, rows, m);
-        case MODE_REACTION:
-            return launch_pdl(k_step1<S, MODE_REACTION>, grid, block, 0, st, u, v, phi, u1, v1,
-                              g.W, g.H, g.pitch, rows, m);
-    }
-    return cudaErrorInvalidValue;
+    return dispatch_mode<S>(mode, md.sr != 0, [&](auto mc) {
+        return launch_pdl(k_step1<S, decltype(mc)::value>, grid, block, 0, st, u, v, phi, u1, v1,
+                          g.W, g.H, g.pitch, rows, m);
+    });
 }
 
 template <typename S>
@@ -353,23 +404,15 @@ cudaError_t launch_stepk_t(int mode, const Planes& g, const ModelD& md, ShapeK s
     const PhiT* phi = static_cast<const PhiT*>(g.phi);
     S* u1 = static_cast<S*>(g.u1);
     S* v1 = static_cast<S*>(g.v1);
-    cudaError_t e;
-    switch (mode) {
-        case MODE_FULL:
-            if ((e = set_stepk_attr<S, MODE_FULL>(smem)) != cudaSuccess) return e;
-            k_stepk<S, MODE_FULL><<<grid, sh.nthreads, smem, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, sh.tx, sh.ty, sh.k, m);
-            break;
-        case MODE_DIFFUSION:
-            if ((e = set_stepk_attr<S, MODE_DIFFUSION>(smem)) != cudaSuccess) return e;
-            k_stepk<S, MODE_DIFFUSION><<<grid, sh.nthreads, smem, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, sh.tx, sh.ty, sh.k, m);
-            break;
-        case MODE_REACTION:
-            if ((e = set_stepk_attr<S, MODE_REACTION>(smem)) != cudaSuccess) return e;
-            k_stepk<S, MODE_REACTION><<<grid, sh.nthreads, smem, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch, sh.tx, sh.ty, sh.k, m);
-            break;
-        default:
-            return cudaErrorInvalidValue;
-    }
+    cudaError_t e = dispatch_mode<S>(mode, md.sr != 0, [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        cudaError_t ea = set_stepk_attr<S, M>(smem);
+        if (ea != cudaSuccess) return ea;
+        k_stepk<S, M><<<grid, sh.nthreads, smem, st>>>(u, v, phi, u1, v1, g.W, g.H, g.pitch,
+                                                        sh.tx, sh.ty, sh.k, m);
+        return cudaSuccess;
+    });
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -158,10 +158,19 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                         cell_update2<MODE>(c2, w2, e2, n2, s2,
                                            make_float2(Q1[l - 1][e], Q1[l - 1][e + 1]),
                                            make_float2(ph[e], ph[e + 1]), m, un, vn);
-                        nu[e] = quantize<S>(un.x);
-                        nu[e + 1] = quantize<S>(un.y);
-                        nv[e] = quantize<S>(vn.x);
-                        nv[e + 1] = quantize<S>(vn.y);
+                        if constexpr ((MODE & MODE_SR) != 0) {
+                            // stochastic rounding of level l (state step0 + l)
+                            const Philox4 rb = sr_pair_bits(m.seed, col >> 1, r, m.step0 + l);
+                            nu[e] = quantize_sr<S>(un.x, rb.x);
+                            nu[e + 1] = quantize_sr<S>(un.y, rb.y);
+                            nv[e] = quantize_sr<S>(vn.x, rb.z);
+                            nv[e + 1] = quantize_sr<S>(vn.y, rb.w);
+                        } else {
+                            nu[e] = quantize<S>(un.x);
+                            nu[e + 1] = quantize<S>(un.y);
+                            nv[e] = quantize<S>(vn.x);
+                            nv[e + 1] = quantize<S>(vn.y);
+                        }
                     }
                 } else {
 #pragma unroll
@@ -237,10 +246,10 @@ k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
 }
 
 // Persistent k-step launch over a batch of grids (see k_step1_batch).
-template <typename S, int K, int N>
+template <typename S, int MODE, int K, int N>
 __global__ void __launch_bounds__(128)
 k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
-               int j)
+               int j, long long sbase)
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
@@ -251,11 +260,12 @@ k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ item
         const GridDesc& d = descs[item.g];
         if (!d.active) continue;
         const int par = (d.par + j) & 1;
-        stream_warp<S, MODE_FULL, K, N>(
+        Model<T> m = model_of<T>(d);
+        m.step0 += sbase;
+        stream_warp<S, MODE, K, N>(
             static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
-            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0, item.y0, item.y1,
-            model_of<T>(d));
+            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0, item.y0, item.y1, m);
     }
 }
 
@@ -271,7 +281,7 @@ struct StreamVec {
 
 template <typename S, int K>
 cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>& m, int rows,
-                            cudaStream_t st)
+                            bool sr, cudaStream_t st)
 {
     using PhiT = typename Traits<S>::PhiT;
     constexpr int N = StreamVec<S, K>::N;
@@ -280,34 +290,40 @@ cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>&
     const int wpb = 4;
     if ((g.H + rows - 1) / rows > 65535) return cudaErrorInvalidValue;
     dim3 grid((nwx + wpb - 1) / wpb, (g.H + rows - 1) / rows);
-    return launch_pdl(k_stepk_stream<S, MODE_FULL, K, N>, grid, dim3(32 * wpb), 0, st,
-                      static_cast<const S*>(g.u), static_cast<const S*>(g.v),
-                      static_cast<const PhiT*>(g.phi), static_cast<S*>(g.u1),
-                      static_cast<S*>(g.v1), g.W, g.H, g.pitch, rows, nwx, m);
+    return dispatch_full<S>(sr, [&](auto mc) {
+        return launch_pdl(k_stepk_stream<S, decltype(mc)::value, K, N>, grid, dim3(32 * wpb), 0,
+                          st, static_cast<const S*>(g.u), static_cast<const S*>(g.v),
+                          static_cast<const PhiT*>(g.phi), static_cast<S*>(g.u1),
+                          static_cast<S*>(g.v1), g.W, g.H, g.pitch, rows, nwx, m);
+    });
 }
 
 template <typename S, int K>
 cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nitems, int j,
-                                  int ctas, cudaStream_t st)
+                                  long long sbase, bool sr, int ctas, cudaStream_t st)
 {
     constexpr int N = StreamVec<S, K>::N;
-    return launch_pdl(k_stream_batch<S, K, N>, dim3(ctas), dim3(128), 0, st, d, items, nitems, j);
+    return dispatch_full<S>(sr, [&](auto mc) {
+        return launch_pdl(k_stream_batch<S, decltype(mc)::value, K, N>, dim3(ctas), dim3(128), 0,
+                          st, d, items, nitems, j, sbase);
+    });
 }
 
 template <typename S>
 cudaError_t launch_batch_stream_t(const GridDesc* d, const Item* items, int nitems, int k,
-                                  int j, int ctas, cudaStream_t st)
+                                  int j, long long sbase, int sr, int ctas, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
     if (ctas < 1) return cudaErrorInvalidValue;
+    const bool r = sr != 0;
     switch (k) {
-        case 2: return launch_stream_batch_k<S, 2>(d, items, nitems, j, ctas, st);
-        case 3: return launch_stream_batch_k<S, 3>(d, items, nitems, j, ctas, st);
-        case 4: return launch_stream_batch_k<S, 4>(d, items, nitems, j, ctas, st);
-        case 5: return launch_stream_batch_k<S, 5>(d, items, nitems, j, ctas, st);
-        case 6: return launch_stream_batch_k<S, 6>(d, items, nitems, j, ctas, st);
-        case 7: return launch_stream_batch_k<S, 7>(d, items, nitems, j, ctas, st);
-        case 8: return launch_stream_batch_k<S, 8>(d, items, nitems, j, ctas, st);
+        case 2: return launch_stream_batch_k<S, 2>(d, items, nitems, j, sbase, r, ctas, st);
+        case 3: return launch_stream_batch_k<S, 3>(d, items, nitems, j, sbase, r, ctas, st);
+        case 4: return launch_stream_batch_k<S, 4>(d, items, nitems, j, sbase, r, ctas, st);
+        case 5: return launch_stream_batch_k<S, 5>(d, items, nitems, j, sbase, r, ctas, st);
+        case 6: return launch_stream_batch_k<S, 6>(d, items, nitems, j, sbase, r, ctas, st);
+        case 7: return launch_stream_batch_k<S, 7>(d, items, nitems, j, sbase, r, ctas, st);
+        case 8: return launch_stream_batch_k<S, 8>(d, items, nitems, j, sbase, r, ctas, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -334,14 +350,15 @@ cudaError_t launch_stream_t(const Planes& g, const ModelD& md, int k, int rows,
 {
     if (rows < 1) return cudaErrorInvalidValue;
     auto m = make_model<S>(md);
+    const bool sr = md.sr != 0;
     switch (k) {
-        case 2: return launch_stream_k<S, 2>(g, m, rows, st);
-        case 3: return launch_stream_k<S, 3>(g, m, rows, st);
-        case 4: return launch_stream_k<S, 4>(g, m, rows, st);
-        case 5: return launch_stream_k<S, 5>(g, m, rows, st);
-        case 6: return launch_stream_k<S, 6>(g, m, rows, st);
-        case 7: return launch_stream_k<S, 7>(g, m, rows, st);
-        case 8: return launch_stream_k<S, 8>(g, m, rows, st);
+        case 2: return launch_stream_k<S, 2>(g, m, rows, sr, st);
+        case 3: return launch_stream_k<S, 3>(g, m, rows, sr, st);
+        case 4: return launch_stream_k<S, 4>(g, m, rows, sr, st);
+        case 5: return launch_stream_k<S, 5>(g, m, rows, sr, st);
+        case 6: return launch_stream_k<S, 6>(g, m, rows, sr, st);
+        case 7: return launch_stream_k<S, 7>(g, m, rows, sr, st);
+        case 8: return launch_stream_k<S, 8>(g, m, rows, sr, st);
     }
     return cudaErrorInvalidValue;
 }

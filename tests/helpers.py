@@ -26,14 +26,16 @@ def round_to_storage(x, prec: str):
 
 
 def gpu_run(pkg, W, H, phi=None, seeds=(), n=0, prec="f64", flags=0, k=1,
-            shape=None, state=None, probes=None, theta=0.3, dtype=np.float64):
+            shape=None, state=None, probes=None, theta=0.3, dtype=np.float64,
+            round_seed=0, chunks=None):
     """Runs n steps on the GPU; returns (u, v, extra) as host arrays.
 
     With ``probes`` (flat indices) it steps one at a time and returns the
     arrival time of each probe (same interpolation rule as the oracle) in
-    extra["t_arr"].
+    extra["t_arr"].  ``chunks`` splits the steps into several rdc_step calls.
     """
-    p = pkg.rdc_params_default(precision=PREC[prec], flags=flags, k_block=k)
+    p = pkg.rdc_params_default(precision=PREC[prec], flags=flags, k_block=k,
+                               round_seed=round_seed)
     if phi is not None:
         phi = np.ascontiguousarray(phi, dtype=np.float64 if prec == "f64" else np.float32)
     h = pkg.rdc_create(W, H, p, phi)
@@ -49,7 +51,10 @@ def gpu_run(pkg, W, H, phi=None, seeds=(), n=0, prec="f64", flags=0, k=1,
             pkg.rdc_set_state(h, *state)
         for (cx, cy, r, val) in seeds:
             pkg.rdc_seed(h, cx, cy, r, val)
-        if probes is None:
+        if probes is None and chunks:
+            for c in chunks:                      # n steps as several calls
+                pkg.rdc_step(h, c)
+        elif probes is None:
             pkg.rdc_step(h, n)
         else:
             pr = np.asarray(probes, dtype=np.int64)

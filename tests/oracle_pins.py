@@ -28,6 +28,13 @@ What each pin fixes:
                        zero-flux (cell-centred mirror) borders.
   conservation         diffusion alone conserves sum(u) (the mirror border
                        has zero flux).
+  round_stoch          stochastic rounding to BF16/FP16: over all 2^16 random
+                       values the mean is exactly x; the results are the two
+                       grid neighbours (NumPy float16, bit truncation for
+                       BF16) split at the stated threshold.
+  philox               Philox4x32-10 is a bijection in each counter word, every
+                       input bit flips about half the output bits, the output
+                       is uniform (no published output values are used).
   symmetry             a seed invariant under the 8 symmetries of the square
                        stays exactly invariant.
   one_d                rows that are identical stay identical and equal the
@@ -326,7 +333,69 @@ def pin_draw(o, om):
     assert o.draw_line(phi, 10.0, 10.0, 10.0, 10.0, 8.0, 1.0) == GAUSS_N[4]
 
 
+def pin_round_stoch(o, om):
+    from fractions import Fraction
+    rng = np.random.default_rng(71)
+    # exact unbiasedness over all 2^16 random values
+    for fmt, xs in (("bf16", [0.3, -1.7e-20, 3.3e25]), ("f16", [0.3, -12.345, 2.5e-3])):
+        for x in xs:
+            x32 = np.float32(x)
+            total = sum(Fraction(o.round_stoch(x32, r, fmt)) for r in range(65536))
+            assert total == Fraction(float(x32)) * 65536, (fmt, x)
+    # the two neighbours, split at the threshold
+    xs = np.concatenate([rng.uniform(0.01, 900.0, 40) * rng.choice([-1, 1], 40),
+                         [9.1e-5, -7.3e-5, 3.3e-5, -1.1e-6]]).astype(np.float32)  # FP16 edges
+    for x in xs:
+        b = int(np.float32(x).view(np.uint32))
+        L = b & 0xFFFF
+        lo = float(np.uint32(b & 0xFFFF0000).view(np.float32))
+        hi = float(np.uint32((b & 0xFFFF0000) + 0x10000).view(np.float32))
+        for r in (0, max(L - 1, 0), L, 65535):
+            assert o.round_stoch(x, r, "bf16") == (hi if r < L else lo), (x, r)
+        lo16 = np.float16(float(x))
+        if abs(float(lo16)) > abs(float(x)):
+            lo16 = np.nextafter(lo16, np.float16(0))
+        hi16 = np.nextafter(lo16, np.float16(np.copysign(np.inf, float(x))))
+        thr = Fraction(abs(float(x)) - abs(float(lo16))) / Fraction(abs(float(hi16)) - abs(float(lo16))) * 65536
+        for r in (0, int(thr), int(thr) + 1, 65535):
+            if 0 <= r < 65536:
+                assert o.round_stoch(x, r, "f16") == float(hi16 if r < thr else lo16), (x, r)
+    assert o.round_stoch(65510.0, 0, "f16") == 65504.0
+    assert o.round_stoch(65520.0, 65535, "f16") == float("inf")
+
+
+def pin_philox(o, om):
+    key = [0x1234567, 0x89ABCDE]
+    for word in range(4):
+        outs = set()
+        for v in range(1024):
+            ctr = [5, 6, 7, 8]
+            ctr[word] = v * 2654435761 % 2**32
+            outs.add(tuple(int(x) for x in o.philox4x32_10(ctr, key)))
+        assert len(outs) == 1024, word
+    rng = np.random.default_rng(72)
+    flips = []
+    for t in range(192):
+        ctr = [int(x) for x in rng.integers(0, 2**32, 4, dtype=np.uint64)]
+        k = [int(x) for x in rng.integers(0, 2**32, 2, dtype=np.uint64)]
+        base = o.philox4x32_10(ctr, k)
+        c2, k2 = list(ctr), list(k)
+        if t < 128:
+            c2[t // 32] ^= 1 << (t % 32)
+        else:
+            k2[(t - 128) // 32] ^= 1 << ((t - 128) % 32)
+        other = o.philox4x32_10(c2, k2)
+        flips.append(sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(base, other)))
+    assert 60.0 < float(np.mean(flips)) < 68.0 and min(flips) > 30, (np.mean(flips), min(flips))
+    counts = np.zeros(256)
+    for i in range(2048):
+        for x in o.philox4x32_10([i, 1, 0, 0], [9, 0]):
+            counts[int(x) >> 24] += 1
+    exp = counts.sum() / 256
+    assert float(((counts - exp) ** 2 / exp).sum()) < 350.0
+
+
 ALL_PINS = [pin_rest_root, pin_rest_fixed_point, pin_jacobian, pin_jacobian_with_mode,
             pin_cosine_modes,
             pin_conservation, pin_symmetry, pin_one_d, pin_uniform_is_single, pin_spike,
-            pin_gauss_circle, pin_health, pin_render, pin_draw]
+            pin_gauss_circle, pin_health, pin_render, pin_draw, pin_round_stoch, pin_philox]

@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(librdc):
 def test_params_default_is_table1(librdc):
     p = librdc.rdc_params_default()
     assert (p.eps, p.f, p.q, p.Du, p.dt, p.dx) == (P.EPS, P.F, P.Q, P.DU, P.DT, P.DX)
-    assert p.precision == 0 and p.flags == 0 and p.k_block == 0 and p.reserved == 0
+    assert p.precision == 0 and p.flags == 0 and p.k_block == 0 and p.round_seed == 0
 
 
 @pytest.mark.parametrize("phi", [0.054, 0.0975, 0.2, 0.05, 0.08, 0.0301, 0.5])
@@ -54,7 +54,9 @@ def test_rest_state_rejects_no_root(librdc):
 @pytest.mark.parametrize("bad", [dict(eps=0.0), dict(q=-1.0), dict(dt=float("nan")),
                                  dict(Du=-0.1), dict(dx=0.0), dict(dt=0.05),
                                  dict(flags=3), dict(precision=7), dict(k_block=9),
-                                 dict(reserved=1), dict(f=0.5)])
+                                 dict(round_seed=1), dict(f=0.5),
+                                 dict(flags=4), dict(flags=4, precision=1), dict(flags=8),
+                                 dict(flags=4 | 3, precision=2)])
 def test_create_validates_params_before_touching_the_device(librdc, bad):
     p = librdc.rdc_params_default(**bad)
     with pytest.raises(librdc.RdcError) as e:
@@ -124,3 +126,30 @@ def test_check_division_validates_before_touching_the_device(librdc):
     for q in (0.0, -0.5, float("nan"), float("inf")):
         assert L.rdc_check_division(q, 0, 0, ctypes.byref(rep)) == librdc.RDC_EINVAL
     assert L.rdc_check_division(0.002, 0, 0, None) == librdc.RDC_EINVAL
+
+
+def test_stochastic_rounding_params_pass_validation(librdc):
+    """RDC_STOCH_ROUND with 16-bit storage and any seed is valid: without a
+    GPU the call gets past validation and fails on the device instead."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a GPU")
+    for prec in (2, 3):
+        for flags in (4, 4 | 1, 4 | 2):
+            p = librdc.rdc_params_default(precision=prec, flags=flags, round_seed=0xDEADBEEF)
+            with pytest.raises(librdc.RdcError) as e:
+                librdc.rdc_create(16, 16, p)
+            assert e.value.status != librdc.RDC_EINVAL
+
+
+def test_stoch_round_sample_validates_before_touching_the_device(librdc):
+    x = np.zeros(4, dtype=np.float32)
+    for prec, row, col0 in ((0, 0, 0), (1, 0, 0), (2, -1, 0), (3, 0, -2)):
+        with pytest.raises(librdc.RdcError) as e:
+            librdc.rdc_stoch_round_sample(prec, 1, 5, row, col0, x)
+        assert e.value.status == librdc.RDC_EINVAL
+
+
+def test_params_reject_unknown_fields(librdc):
+    with pytest.raises(TypeError):
+        librdc.rdc_params_default(reserved=0)

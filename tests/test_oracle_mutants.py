@@ -39,6 +39,15 @@ MUTANTS = [
     ("seed_strict", "if (dy * dy + dx * dx <= r2)", "if (dy * dy + dx * dx < r2)"),
     ("seed_axes_swapped", "double dy = (double)i - cy;", "double dy = (double)i - cx;"),
     ("health_no_pole", "|| (u + q) <= 0.0;", "|| 0;"),
+    ("stoch_threshold_le", "((double)r16 < ldexp(frac, 16))", "((double)r16 <= ldexp(frac, 16))"),
+    ("stoch_bf16_precision", "const int mant = fmt == 0 ? 7 : 10;",
+     "const int mant = fmt == 0 ? 8 : 10;"),
+    ("stoch_f16_subnormal_edge", "const int emin = fmt == 0 ? -126 : -14;",
+     "const int emin = fmt == 0 ? -126 : -13;"),
+    ("stoch_round_down_only", "? lo + sp : lo;", "? lo : lo;"),
+    ("philox_key_dropped", "^ c[1] ^ k0;", "^ c[1];"),
+    ("philox_one_round", "round < 10; ++round", "round < 1; ++round"),
+    ("philox_word_reused", "^ c[3] ^ k1;", "^ c[1] ^ k1;"),
 ]
 
 
