@@ -120,9 +120,9 @@ typedef struct {
     int32_t flags;     /* RDC_DIFFUSION_ONLY | RDC_REACTION_ONLY (not both),
                           | RDC_STOCH_ROUND */
     int32_t k_block;   /* Euler steps fused per launch (temporal blocking):
-                          0 = library default (for grids of >= 2^20
-                          cells in the full model: 6 with FP32 storage, 4
-                          with 16-bit storage; else 1; see rdc_tune),
+                          0 = library default (4 for FP32-compute grids of
+                          >= 2^20 cells in the full model, else 1; see
+                          rdc_tune),
                           1 = one step per launch,
                           2..8 = k steps per launch.  Results are bitwise
                           identical for every k. */

@@ -269,13 +269,13 @@ static void default_shapes(rdc_sim* s)
         s->shapek = ShapeK{64, 32, 1, 256};
     // k_block = 0: temporal blocking for grids of a million cells or more in
     // the FP32-compute modes, where HBM would otherwise bound a single step
-    // (measured best at 8192^2: 6 steps per launch with FP32 storage, 4 with
-    // 16-bit storage); FP64 is bound by its arithmetic, so one step per
-    // launch.  rdc_tune measures instead of guessing.
+    // (measured best at 8192^2: 4 steps per launch); FP64 is bound by its
+    // arithmetic, so one step per launch.  rdc_tune measures instead of
+    // guessing.
     int kdef = 1;
     if (s->p.k_block == 0 && s->prec != P_F64 && s->mode == MODE_FULL &&
         (int64_t)s->W * s->H >= (1 << 20))
-        kdef = s->prec == P_F32 ? 6 : 4;
+        kdef = 4;
     s->shapek.k = s->p.k_block == 0 ? kdef : s->p.k_block;
     s->shapek.variant = 0;
     // rows per CTA of the streamed kernel: long enough that the 2k rows of

@@ -61,6 +61,15 @@ struct VecN {
     }
 };
 
+// Mirror image of index x in [0, n) under the cell-centred zero-flux
+// border: -1 -> 0, -2 -> 1, n -> n - 1, ... (repeated for grids narrower
+// than the reach).
+__device__ __forceinline__ int reflect_index(int x, int n)
+{
+    while (x < 0 || x >= n) x = (x < 0) ? -1 - x : 2 * n - 1 - x;
+    return x;
+}
+
 template <typename S, int K, int N>
 struct StreamGeom {
     static constexpr int HALO = (K + N - 1) / N * N;  // overlap per side, columns
@@ -85,7 +94,7 @@ struct StreamGeom {
 // levels' arithmetic; warp-uniform branches there measured slower.  For
 // K >= 4 the row loop is unrolled three times, which turns the three-row
 // register rotation into renaming.
-template <typename S, int MODE, int K, int N>
+template <typename S, int MODE, int K, int N, bool GH>
 __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                                                  const S* __restrict__ v,
                                                  const typename Traits<S>::PhiT* __restrict__ phi,
@@ -94,13 +103,48 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                                                  int y1, const Model<typename Traits<S>::T>& m)
 {
     using T = typename Traits<S>::T;
+    using PhiT = typename Traits<S>::PhiT;
     using G = StreamGeom<S, K, N>;
+    // GHOST: cells beyond the borders are loaded as mirror images of the cells
+    // inside (rows and columns), so the level loop needs no border selects.
+    // Addition is commutative, so a mirrored ghost cell evolves exactly like
+    // its image and every valid cell gets the same bits as with the selects.
+    // Not with stochastic rounding (a ghost would draw its own random bits).
+    constexpr bool GHOST = GH && (MODE & MODE_SR) == 0;
     const int lane = threadIdx.x & 31;
     const int a = col_out - G::HALO;
     const int cl = a + lane * N;
     const bool in_grid = (cl >= 0) && (cl < W);
-    const int t0 = max(y0 - K, 0);
+    const bool plain = (cl >= 0) && (cl + N <= W);  // every cell of the lane inside
+    int srcc[N];                                     // mirrored source columns
+#pragma unroll
+    for (int e = 0; e < N; ++e) srcc[e] = reflect_index(cl + e, W);
+    const int t0 = GHOST ? y0 - K : max(y0 - K, 0);
     const int t_end = y1 - 1 + K;
+    // u, v, phi of row tl (mirrored rows and columns with GHOST; zeros outside
+    // the grid otherwise)
+    auto load_row = [&](int tl, T (&ru)[N], T (&rv)[N], T (&rp)[N]) {
+        if constexpr (GHOST) {
+            const int64_t ro = (int64_t)reflect_index(tl, H) * pitch;
+            if (plain) {
+                VecN<S, N>::load(u + ro + cl, ru);
+                VecN<S, N>::load(v + ro + cl, rv);
+                VecN<PhiT, N>::load(phi + ro + cl, rp);
+            } else {
+#pragma unroll
+                for (int e = 0; e < N; ++e) {
+                    ru[e] = widen(u[ro + srcc[e]]);
+                    rv[e] = widen(v[ro + srcc[e]]);
+                    rp[e] = (T)phi[ro + srcc[e]];
+                }
+            }
+        } else if (tl < H && in_grid) {
+            const int64_t o = (int64_t)tl * pitch + cl;
+            VecN<S, N>::load(u + o, ru);
+            VecN<S, N>::load(v + o, rv);
+            VecN<PhiT, N>::load(phi + o, rp);
+        }
+    };
     T P0[K][N], P1[K][N], P2[K][N], Q0[K][N], Q1[K][N];
     T F[K][N];  // F[j]: phi of row t - 1 - j, loaded with that row's u and v
 #pragma unroll
@@ -116,12 +160,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     T pu[N], pv[N], pp[N];
 #pragma unroll
     for (int e = 0; e < N; ++e) pu[e] = pv[e] = pp[e] = T(0);
-    if (AHEAD && t0 < H && in_grid) {
-        const int64_t o = (int64_t)t0 * pitch + cl;
-        VecN<S, N>::load(u + o, pu);
-        VecN<S, N>::load(v + o, pv);
-        VecN<typename Traits<S>::PhiT, N>::load(phi + o, pp);
-    }
+    if (AHEAD) load_row(t0, pu, pv, pp);
     constexpr int UNROLL = (K >= 4) ? 3 : 1;
 #pragma unroll UNROLL
     for (int t = t0; t <= t_end; ++t) {
@@ -136,12 +175,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                 nphi[e] = pp[e];
                 pu[e] = pv[e] = pp[e] = T(0);
             }
-            if (tl <= t_end && tl < H && in_grid) {
-                const int64_t o = (int64_t)tl * pitch + cl;
-                VecN<S, N>::load(u + o, pu);
-                VecN<S, N>::load(v + o, pv);
-                VecN<typename Traits<S>::PhiT, N>::load(phi + o, pp);
-            }
+            if (tl <= t_end) load_row(tl, pu, pv, pp);
             if constexpr (!AHEAD) {
 #pragma unroll
                 for (int e = 0; e < N; ++e) {
@@ -165,7 +199,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
             const T esh = __shfl_down_sync(0xffffffffu, P1[l - 1][0], 1);
             {
                 const T (&ph)[N] = F[l - 1];
-                const bool top = (r == 0), bottom = (r == H - 1);
+                const bool top = !GHOST && (r == 0), bottom = !GHOST && (r == H - 1);
                 if constexpr (sizeof(T) == 4 && N % 2 == 0) {
                     // FP32 compute: neighbouring cells in pairs (cell_update2).
                     // The border selects also assemble the west and east pairs.
@@ -176,9 +210,10 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                         const float wr = (e == 0) ? wsh : P1[l - 1][e - 1];
                         const float er = (e + 2 == N) ? esh : P1[l - 1][e + 2];
                         const float2 c2 = make_float2(c0, c1);
-                        const float2 w2 = make_float2(col <= 0 ? c0 : wr, col + 1 <= 0 ? c1 : c0);
-                        const float2 e2 = make_float2(col >= W - 1 ? c0 : c1,
-                                                      col + 1 >= W - 1 ? c1 : er);
+                        const float2 w2 = make_float2(!GHOST && col <= 0 ? c0 : wr,
+                                                      !GHOST && col + 1 <= 0 ? c1 : c0);
+                        const float2 e2 = make_float2(!GHOST && col >= W - 1 ? c0 : c1,
+                                                      !GHOST && col + 1 >= W - 1 ? c1 : er);
                         const float2 n2 = top ? c2 : make_float2(P2[l - 1][e], P2[l - 1][e + 1]);
                         const float2 s2 =
                             bottom ? c2 : make_float2(P0[l - 1][e], P0[l - 1][e + 1]);
@@ -207,8 +242,8 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                         const T c = P1[l - 1][e];
                         T w = (e == 0) ? wsh : P1[l - 1][e - 1];
                         T ea = (e == N - 1) ? esh : P1[l - 1][e + 1];
-                        if (col <= 0) w = c;
-                        if (col >= W - 1) ea = c;
+                        if (!GHOST && col <= 0) w = c;
+                        if (!GHOST && col >= W - 1) ea = c;
                         const T n = top ? c : P2[l - 1][e];
                         const T s = bottom ? c : P0[l - 1][e];
                         T un, vn;
@@ -247,15 +282,22 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     }
 }
 
-template <typename S, int MODE, int K, int N>
+template <typename S, int MODE, int K, int N, bool GH>
 __device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __restrict__ v,
                                             const typename Traits<S>::PhiT* __restrict__ phi,
                                             S* __restrict__ u1, S* __restrict__ v1, int W,
                                             int H, int64_t pitch, int col_out, int y0, int y1,
                                             const Model<typename Traits<S>::T>& m)
 {
-    stream_warp_impl<S, MODE, K, N>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
+    stream_warp_impl<S, MODE, K, N, GH>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
 }
+
+// Mirrored ghost cells instead of border selects: measured faster for the
+// single-grid FP32 kernel at K >= 4 (K = 4: 724 -> 805, K = 6: 760 -> 786 G
+// cell-updates/s at 8192^2), slower for K <= 3, 16-bit storage and the
+// batched kernel, whose register budgets it exceeds.
+template <typename S, int K>
+constexpr bool stream_ghost() { return sizeof(S) == 4 && K >= 4; }
 
 template <typename S, int MODE, int K, int N>
 __global__ void __launch_bounds__(128)
@@ -269,7 +311,7 @@ k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
     const int wx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wx >= nwarps_x) return;                       // whole warps only
     const int y0 = blockIdx.y * rows;
-    stream_warp<S, MODE, K, N>(u, v, phi, u1, v1, W, H, pitch, wx * G::OUTC, y0,
+    stream_warp<S, MODE, K, N, stream_ghost<S, K>()>(u, v, phi, u1, v1, W, H, pitch, wx * G::OUTC, y0,
                                min(y0 + rows, H), m);
 }
 
@@ -290,7 +332,7 @@ k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ item
         const int par = (d.par + j) & 1;
         Model<T> m = model_of<T>(d);
         m.step0 += sbase;
-        stream_warp<S, MODE, K, N>(
+        stream_warp<S, MODE, K, N, false>(
             static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
             static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0, item.y0, item.y1, m);

@@ -51,6 +51,7 @@ def _oracle_cell(orc, i, j, n):
 
 @pytest.mark.parametrize("prec,k,n,tol", [("f64", 1, 3, 0.0), ("f64", 3, 3, 0.0),
                                           ("f32", 1, 4, 2e-6), ("f32", 4, 4, 2e-6),
+                                          ("f32", 6, 6, 3e-6), ("f32", 0, 12, 5e-6),
                                           ("bf16", 4, 4, 2e-2), ("f16", 1, 4, 5e-3)])
 def test_fullsize_sampled(gpu, orc, prec, k, n, tol):
     p = gpu.rdc_params_default(precision=PREC[prec], k_block=k)
