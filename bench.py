@@ -38,6 +38,7 @@ EULER_STEPS = 10000
 N_DISKS = 200
 DISK_SEED = 3
 BYTES_PER_CELL = {"f32": 20, "bf16": 12, "f16": 12, "f64": 40}
+STORAGE_TYPE = {"f32": "float", "f64": "double", "bf16": "__nv_bfloat16", "f16": "__half"}
 METRIC = "GCUPS (cell-updates/s)"
 
 
@@ -246,6 +247,8 @@ def main():
                     help="Euler steps per launch of the timed kernel (1 = single-step kernel)")
     ap.add_argument("--grid", type=int, default=None,
                     help="square grid size (default 8192); smaller sizes are for profiling")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "f16"],
+                    help="storage of the timed run (default f32; the others are for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -264,7 +267,7 @@ def main():
     # a dedicated stream: the simulation and the CUDA events share it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    p = pkg.rdc_params_default(precision=pkg.RDC_F32, k_block=args.kblock)
+    p = pkg.rdc_params_default(precision=args.precision, k_block=args.kblock)
     h = pkg.rdc_create(W, H, p, None, stream.cuda_stream)
     disks = ri.random_disks(DISK_SEED, N_DISKS, W, H)
     nE = args.euler_steps
@@ -310,7 +313,7 @@ def main():
     peak, peak_kind = _peaks()
     per_launch_s = step_kernel_s / launches
     # one launch moves the state once whatever k is (k Euler steps per launch)
-    bytes_per_launch = BYTES_PER_CELL["f32"] * W * H
+    bytes_per_launch = BYTES_PER_CELL[args.precision] * W * H
     achieved = bytes_per_launch / per_launch_s / 1e9
 
     extras = {}
@@ -343,19 +346,21 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
+                "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": f"oregonator_{W}x{H}_phi0.054_200disks",
                            "grid": [W, H], "euler_steps_per_bench_step": nE,
                            "kernel": ("single-step (k=1)" if args.kblock == 1 else
                                       f"temporally blocked (k={args.kblock})"),
-                           "precision": "f32",
+                           "precision": args.precision,
                            "l2": "inputs larger than L2 (1.34 GB state), no flush"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": peak_kind,
-                             "traffic": _traffic("k_step1<float>", W * H) if args.kblock == 1 else None,
-                             "kernel": "k_step1<float>" if args.kblock == 1 else "k_stepk_stream<float>",
-                             "bytes_per_cell_update": BYTES_PER_CELL["f32"],
+                             "traffic": (_traffic("k_step1<float>", W * H)
+                                         if args.kblock == 1 and args.precision == "f32" else None),
+                             "kernel": f"{'k_step1' if args.kblock == 1 else 'k_stepk_stream'}"
+                                       f"<{STORAGE_TYPE[args.precision]}>",
+                             "bytes_per_cell_update": BYTES_PER_CELL[args.precision],
                              "launch_us": per_launch_s * 1e6},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches + args.steps * (N_DISKS + 1)),
