@@ -331,7 +331,8 @@ def main():
         modes["bf16_stoch"] = _mode_gcups(pkg, stream, "bf16", 1, 1000, flags=4)
         modes["bf16_stoch_tuned"] = _tuned(pkg, stream, "bf16", flags=4)
         extras = {"temporal_blocking_gcups": tb, "tuned_f32": tuned, "storage_modes_gcups": modes,
-                  "batch_sweep": _batch_sweep(pkg, stream), "serving": _serving(pkg)}
+                  "batch_sweep": _batch_sweep(pkg, stream), "serving": _serving(pkg),
+                  "render": _render(pkg, stream, h)}
     e2e = None if args.no_extras else _e2e(pkg, stream, h, disks, nE, args)
 
     pkg.rdc_destroy(h)
@@ -417,6 +418,28 @@ def _mode_gcups(pkg, stream, mode, k, n, krows=None, flags=0):
         return W * H * n / (a.elapsed_time(b) / 1e3) / 1e9
     finally:
         pkg.rdc_destroy(h)
+
+
+def _render(pkg, stream, h, reps=20):
+    """Colour map of the bench grid into a device RGBA8 buffer (reads u, v and
+    phi, 12 B per pixel in FP32, writes 4 B): pixels per second and the
+    fraction of the measured copy peak."""
+    import torch
+    out = torch.empty((H, W, 4), dtype=torch.uint8, device="cuda")
+    pkg.rdc_render(h, out=out)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        pkg.rdc_render(h, out=out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3 / reps
+    peak, kind = _peaks()
+    gbs = 16.0 * W * H / sec / 1e9
+    return {"gpix_per_s": W * H / sec / 1e9, "ms_per_frame": sec * 1e3, "gb_s": gbs,
+            "frac": gbs / peak, "peak_kind": kind, "bytes_per_pixel": 16}
 
 
 def _batch_sweep(pkg, stream, steps=5000):

@@ -36,6 +36,7 @@ class Session:
     height: int
     phi: np.ndarray | None = None          # H x W float32 map, or None (uniform)
     eps: float | None = None
+    round_seed: int = 0                     # key of the stochastic rounding (flags RDC_STOCH_ROUND)
     frames: int = 10                        # frames the session will request
     touches: list = dataclasses.field(default_factory=list)  # per frame (cx, cy, r, value) or None
     # filled in by the server
@@ -66,12 +67,14 @@ class Frame:
 class Server:
     def __init__(self, precision=C.RDC_F32, k_block: int = 2, steps_per_frame: int = 50,
                  memory_budget: int | None = None, max_sessions: int = 1 << 30,
-                 stream=None, graphs: bool = False):
+                 stream=None, graphs: bool = False, flags: int = 0):
+        """flags: 0 or RDC_STOCH_ROUND (16-bit storage), for every session."""
         import torch
         self.torch = torch
         self.precision = precision
+        self.flags = int(flags)
         self.steps = int(steps_per_frame)
-        self.params = C.rdc_params_default(precision=precision, k_block=k_block)
+        self.params = C.rdc_params_default(precision=precision, k_block=k_block, flags=self.flags)
         if stream is None:
             stream = torch.cuda.Stream()
         self.stream = stream
@@ -105,7 +108,9 @@ class Server:
             need = s.state_bytes(self.precision)
             if self.used + need > self.budget:
                 break
-            p = C.rdc_params_default(precision=self.precision, k_block=self.params.k_block)
+            p = C.rdc_params_default(precision=self.precision, k_block=self.params.k_block,
+                                     flags=self.flags,
+                                     round_seed=s.round_seed if self.flags else 0)
             if s.eps is not None:
                 p.eps = s.eps
             s.slot = C.rdc_batch_add(self.batch, s.width, s.height, p, s.phi)

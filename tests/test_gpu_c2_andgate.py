@@ -22,10 +22,11 @@ def _circuit():
     return ri.and_gate(N, N, arm=150, out_len=80)
 
 
-def _max_at_output(pkg, c, fire, prec):
+def _max_at_output(pkg, c, fire, prec, flags=0, round_seed=0):
     """Largest u seen at the output probe, sampled every SAMPLE steps."""
     phi = c.phi if prec == "f64" else c.phi.astype(np.float32)
-    p = pkg.rdc_params_default(precision=PREC[prec], k_block=0 if prec != "f64" else 1)
+    p = pkg.rdc_params_default(precision=PREC[prec], k_block=0 if prec != "f64" else 1,
+                               flags=flags, round_seed=round_seed)
     h = pkg.rdc_create(N, N, p, phi)
     best = -1.0
     try:
@@ -69,3 +70,21 @@ def test_c2_bf16_reported(gpu, record_property):
              for f in ([], ["A"], ["B"], ["A", "B"])}
     record_property("bf16_truth_table", table)
     print("bf16 AND truth table at 1024^2:", table)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_c2_stochastic_rounding_truth_table(gpu, prec, record_property):
+    """16-bit storage with stochastic rounding (RDC_STOCH_ROUND) on the same
+    circuit, three keys: the AND truth table holds for each.  (BF16 with
+    round-to-nearest loses it: v stagnates and the colliding fronts do not
+    cross the band; the runs are deterministic for a given key.)"""
+    c = _circuit()
+    tables = {}
+    for seed in (1, 2, 3):
+        tables[seed] = {"".join(f) or "-": bool(_max_at_output(gpu, c, f, prec, flags=4,
+                                                               round_seed=seed) > 0.3)
+                        for f in ([], ["A"], ["B"], ["A", "B"])}
+    record_property(f"{prec}_stochastic_truth_tables", tables)
+    print(f"{prec} + stochastic rounding AND truth tables at 1024^2:", tables)
+    for seed, t in tables.items():
+        assert t == {"-": False, "A": False, "B": False, "AB": True}, (seed, t)

@@ -30,8 +30,9 @@ def _sessions(serve, n, seed=5, frames=6):
     return out
 
 
-def _alone(pkg, s, steps):
-    p = pkg.rdc_params_default(precision=0)
+def _alone(pkg, s, steps, precision=0, flags=0):
+    p = pkg.rdc_params_default(precision=precision, flags=flags,
+                               round_seed=s.round_seed if flags else 0)
     h = pkg.rdc_create(s.width, s.height, p, s.phi)
     try:
         for f in range(s.frames):
@@ -135,4 +136,31 @@ def test_serving_eviction_mid_stream(gpu):
             continue
         u, v = finals[s.sid]
         ua, va = _alone(gpu, s, 12)
+        assert np.array_equal(u, ua) and np.array_equal(v, va), s.sid
+
+
+def test_serving_stochastic_rounding_mix_equals_alone(gpu):
+    """BF16 storage with stochastic rounding, one key per session: the mix
+    gives each session the bits it gets alone (the rounding depends only on
+    the session's key, the cell and the step)."""
+    from paper_1901_06535_gb300 import serve
+    sessions = _sessions(serve, 8, seed=31, frames=4)
+    for s in sessions:
+        s.round_seed = 1000 + s.sid
+    srv = serve.Server(precision=2, k_block=4, steps_per_frame=14, flags=4)
+    finals = {}
+    orig_leave = srv._leave
+
+    def leave(s):
+        finals[s.sid] = srv.read(s)
+        orig_leave(s)
+
+    srv._leave = leave
+    try:
+        serve.run_workload(sessions, [0.001 * i for i in range(len(sessions))], srv)
+    finally:
+        srv.close()
+    for s in sessions:
+        u, v = finals[s.sid]
+        ua, va = _alone(gpu, s, 14, precision=2, flags=4)
         assert np.array_equal(u, ua) and np.array_equal(v, va), s.sid
