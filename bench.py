@@ -249,6 +249,8 @@ def main():
                     help="square grid size (default 8192); smaller sizes are for profiling")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "bf16", "f16"],
                     help="storage of the timed run (default f32; the others are for profiling)")
+    ap.add_argument("--stoch", action="store_true",
+                    help="stochastic rounding of the 16-bit storage (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -267,7 +269,8 @@ def main():
     # a dedicated stream: the simulation and the CUDA events share it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    p = pkg.rdc_params_default(precision=args.precision, k_block=args.kblock)
+    p = pkg.rdc_params_default(precision=args.precision, k_block=args.kblock,
+                               flags=4 if args.stoch else 0)
     h = pkg.rdc_create(W, H, p, None, stream.cuda_stream)
     disks = ri.random_disks(DISK_SEED, N_DISKS, W, H)
     nE = args.euler_steps

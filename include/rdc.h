@@ -89,12 +89,13 @@ extern "C" {
  * and lo otherwise, r16 being 16 random bits (non-finite x, and FP16 beyond
  * 65504, round to nearest).  The expected stored value is then x, so small
  * per-step increments (dt (u - v) is often below half a BF16 spacing of v)
- * survive on average instead of being lost every step.  r16 is the top half
- * of a word of Philox4x32-10 (Salmon et al., SC'11) with counter
- * (column / 2, row, step index mod 2^32, step index / 2^32) and key
- * (round_seed, 0): words 0 and 2 for the u and v of the even column of the
- * pair, words 1 and 3 for the odd column.  The step index is the index of
- * the state being written (steps since rdc_create or rdc_reset_rest).
+ * survive on average instead of being lost every step.  The random bits
+ * come from Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (column / 4, row, step index mod 2^32, step index / 2^32) and key
+ * (round_seed, 0): word (column mod 4) of the output, whose top 16 bits are
+ * r16 for the cell's u and whose low 16 bits are r16 for its v.  The step
+ * index is the index of the state being written (steps since rdc_create or
+ * rdc_reset_rest).
  * Results are deterministic and identical for every k_block, launch shape
  * and batch; rdc_stoch_round_sample exposes the rounding.  Not available in
  * rdc_step_noalloc.

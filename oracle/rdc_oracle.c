@@ -500,22 +500,22 @@ float orc_round_stoch(float x, uint32_t r16, int32_t fmt)
 }
 
 /* The rounding of the u (out_u) and the v (out_v) of cells (col0 + i, row)
- * for the state with index `step`, key seed: counter (col / 2, row, step mod
- * 2^32, step / 2^32), key (seed, 0); words 0, 2 for an even column, 1, 3 for
- * an odd one; each word's top 16 bits. */
+ * for the state with index `step`, key seed: counter (col / 4, row, step mod
+ * 2^32, step / 2^32), key (seed, 0); word col mod 4 of the output, its top
+ * 16 bits for u and its low 16 bits for v. */
 void orc_round_stoch_cells(int64_t n, const float* x, uint32_t seed, int64_t step, int32_t row,
                            int32_t col0, int32_t fmt, float* out_u, float* out_v)
 {
     for (int64_t i = 0; i < n; ++i) {
         const int64_t col = (int64_t)col0 + i;
         const uint64_t s = (uint64_t)step;
-        const uint32_t ctr[4] = {(uint32_t)(col / 2), (uint32_t)row, (uint32_t)s,
+        const uint32_t ctr[4] = {(uint32_t)(col / 4), (uint32_t)row, (uint32_t)s,
                                  (uint32_t)(s >> 32)};
         const uint32_t key[2] = {seed, 0u};
         uint32_t w[4];
         orc_philox4x32_10(ctr, key, w);
-        const int odd = (int)(col % 2);
-        out_u[i] = orc_round_stoch(x[i], w[odd] >> 16, fmt);
-        out_v[i] = orc_round_stoch(x[i], w[2 + odd] >> 16, fmt);
+        const uint32_t word = w[col % 4];
+        out_u[i] = orc_round_stoch(x[i], word >> 16, fmt);
+        out_v[i] = orc_round_stoch(x[i], word & 0xFFFFu, fmt);
     }
 }

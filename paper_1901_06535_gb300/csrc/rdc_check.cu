@@ -142,9 +142,9 @@ __global__ void k_sr_sample(const float* __restrict__ x, int n, unsigned seed, l
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int col = col0 + i;
-    const Philox4 rb = sr_pair_bits(seed, col >> 1, row, step);
-    uo[i] = quantize_sr<S>(x[i], (col & 1) ? rb.y : rb.x);
-    vo[i] = quantize_sr<S>(x[i], (col & 1) ? rb.w : rb.z);
+    const unsigned w = sr_word(sr_quad_bits(seed, col >> 2, row, step), col & 3);
+    uo[i] = quantize_sr<S>(x[i], w);
+    vo[i] = quantize_sr<S>(x[i], w << 16);
 }
 
 }  // namespace

@@ -128,14 +128,18 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
                 }
             }
             if constexpr ((MODE & MODE_SR) != 0) {
-                // stochastic rounding of the new state (index step0 + 1)
+                // stochastic rounding of the new state (index step0 + 1); a
+                // lane's VEC cells are VEC / 4 whole quads
+                static_assert(VEC % 4 == 0, "quads of cells");
 #pragma unroll
-                for (int e = 0; e < VEC; e += 2) {
-                    const Philox4 rb = sr_pair_bits(m.seed, (col0 + e) >> 1, r, m.step0 + 1);
-                    ou[e] = quantize_sr<S>(ou[e], rb.x);
-                    ou[e + 1] = quantize_sr<S>(ou[e + 1], rb.y);
-                    ov[e] = quantize_sr<S>(ov[e], rb.z);
-                    ov[e + 1] = quantize_sr<S>(ov[e + 1], rb.w);
+                for (int e = 0; e < VEC; e += 4) {
+                    const Philox4 rb = sr_quad_bits(m.seed, (col0 + e) >> 2, r, m.step0 + 1);
+                    const unsigned w[4] = {rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        ou[e + i] = quantize_sr<S>(ou[e + i], w[i]);
+                        ov[e + i] = quantize_sr<S>(ov[e + i], w[i] << 16);
+                    }
                 }
             }
             if (col0 + VEC <= W) {
@@ -160,9 +164,11 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
 }
 
 // At most 72 registers: the 16-bit-storage instantiations (8 cells per
-// thread) would otherwise take 73 and fit one CTA fewer per SM.
+// thread) would otherwise take 73 and fit one CTA fewer per SM.  The
+// stochastic-rounding ones need more for the random words (capped at 72
+// they spilled to local memory).
 template <typename S, int MODE>
-__global__ void __maxnreg__(72)
+__global__ void __maxnreg__((MODE & MODE_SR) ? 128 : 72)
 k_step1(const S* __restrict__ u, const S* __restrict__ v,
         const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
         S* __restrict__ v1, int W, int H, int64_t pitch, int rows,
@@ -288,9 +294,10 @@ k_stepk(const S* __restrict__ u, const S* __restrict__ v,
                 T un, vn;
                 cell_update<MODE>(c, w, e, n, so_v, vs[i], ps[i], m, un, vn);
                 if constexpr ((MODE & MODE_SR) != 0) {
-                    const Philox4 rb = sr_pair_bits(m.seed, gx >> 1, gy, m.step0 + s);
-                    nxt[i] = quantize_sr<S>(un, (gx & 1) ? rb.y : rb.x);
-                    vs[i] = quantize_sr<S>(vn, (gx & 1) ? rb.w : rb.z);
+                    const unsigned w =
+                        sr_word(sr_quad_bits(m.seed, gx >> 2, gy, m.step0 + s), gx & 3);
+                    nxt[i] = quantize_sr<S>(un, w);
+                    vs[i] = quantize_sr<S>(vn, w << 16);
                 } else {
                     nxt[i] = quantize<S>(un);
                     vs[i] = quantize<S>(vn);

@@ -200,6 +200,12 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
             {
                 const T (&ph)[N] = F[l - 1];
                 const bool top = !GHOST && (r == 0), bottom = !GHOST && (r == H - 1);
+                // stochastic rounding: the random words of the lane's quad (its N
+                // cells lie in one quad: N = 2 starts at an even column, N = 4 at
+                // a multiple of 4)
+                Philox4 rb{0u, 0u, 0u, 0u};
+                if constexpr ((MODE & MODE_SR) != 0)
+                    rb = sr_quad_bits(m.seed, cl >> 2, r, m.step0 + l);
                 if constexpr (sizeof(T) == 4 && N % 2 == 0) {
                     // FP32 compute: neighbouring cells in pairs (cell_update2).
                     // The border selects also assemble the west and east pairs.
@@ -223,11 +229,12 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                                            make_float2(ph[e], ph[e + 1]), m, un, vn);
                         if constexpr ((MODE & MODE_SR) != 0) {
                             // stochastic rounding of level l (state step0 + l)
-                            const Philox4 rb = sr_pair_bits(m.seed, col >> 1, r, m.step0 + l);
-                            nu[e] = quantize_sr<S>(un.x, rb.x);
-                            nu[e + 1] = quantize_sr<S>(un.y, rb.y);
-                            nv[e] = quantize_sr<S>(vn.x, rb.z);
-                            nv[e + 1] = quantize_sr<S>(vn.y, rb.w);
+                            const bool hi = (col & 2) != 0;  // words 2, 3 of the quad
+                            const unsigned w0 = hi ? rb.z : rb.x, w1 = hi ? rb.w : rb.y;
+                            nu[e] = quantize_sr<S>(un.x, w0);
+                            nu[e + 1] = quantize_sr<S>(un.y, w1);
+                            nv[e] = quantize_sr<S>(vn.x, w0 << 16);
+                            nv[e + 1] = quantize_sr<S>(vn.y, w1 << 16);
                         } else {
                             nu[e] = quantize<S>(un.x);
                             nu[e + 1] = quantize<S>(un.y);

@@ -160,12 +160,13 @@ def test_philox_output_is_uniform(orc):
 
 
 def test_cells_use_the_documented_words(orc):
-    """round_stoch_cells: even column -> words 0 (u) and 2 (v), odd -> 1, 3,
-    counter (col // 2, row, step low, step high), key (seed, 0)."""
+    """round_stoch_cells: counter (col // 4, row, step low, step high), key
+    (seed, 0); word col % 4, top 16 bits for u, low 16 bits for v."""
     x = np.float32(0.3)
     seed, step, row = 99, (5 << 32) + 17, 4
-    u, v = orc.round_stoch_cells(np.full(4, x), seed, step, row, 6, "bf16")
-    for i, col in enumerate(range(6, 10)):
-        w = orc.philox4x32_10([col // 2, row, step & 0xFFFFFFFF, step >> 32], [seed, 0])
-        assert u[i] == np.float32(orc.round_stoch(x, int(w[col % 2]) >> 16, "bf16"))
-        assert v[i] == np.float32(orc.round_stoch(x, int(w[2 + col % 2]) >> 16, "bf16"))
+    u, v = orc.round_stoch_cells(np.full(8, x), seed, step, row, 6, "bf16")
+    for i, col in enumerate(range(6, 14)):
+        w = orc.philox4x32_10([col // 4, row, step & 0xFFFFFFFF, step >> 32], [seed, 0])
+        word = int(w[col % 4])
+        assert u[i] == np.float32(orc.round_stoch(x, word >> 16, "bf16"))
+        assert v[i] == np.float32(orc.round_stoch(x, word & 0xFFFF, "bf16"))
