@@ -1,18 +1,20 @@
 // k_stepk_stream: K explicit Euler steps of Eq. 1 per launch (temporal
 // blocking) with every intermediate time level held in registers.
 //
-// Each warp owns a strip of 32 * VEC columns (one VEC-cell vector per lane)
-// and marches down a chunk of rows.  At iteration t it loads row t of u, v
-// (time level 0) and, for l = 1..K, computes row t - l of time level l from
-// rows t-l-1, t-l, t-l+1 of level l-1 -- a wavefront in (row, time).  Each
-// level keeps the last three u rows and two v rows it produced in registers;
-// only level K is written to memory.  East/west neighbours come from the
-// adjacent lanes by shuffles, so a level is valid one column less on each side
-// than the level before: warps overlap by HALO = roundup(K, VEC) columns per
-// side (a multiple of VEC keeps every vector 16/8-byte aligned) and each
-// writes only its 32 * VEC - 2 * HALO interior columns.  Chunks overlap by K
-// rows above and below for the same reason.  At the grid's own borders the
-// mirror rule needs no outside data, so those cells are valid at every level.
+// Each warp owns a strip of 32 * N columns (N cells per lane) and marches
+// down a chunk of rows.  At iteration t it takes row t of u, v and phi (time
+// level 0) and, for l = 1..K, computes row t - l of time level l from rows
+// t-l-1, t-l, t-l+1 of level l-1 -- a wavefront in (row, time).  Each level
+// keeps the last three u rows and two v rows it produced in registers, phi
+// travels down the levels in a register queue, and only level K is written
+// to memory.  East/west neighbours come from the adjacent lanes by shuffles,
+// so a level is valid one column less on each side than the level before:
+// warps overlap by HALO = roundup(K, N) columns per side (a multiple of N
+// keeps every vector aligned) and each writes only its 32 * N - 2 * HALO
+// interior columns.  Chunks overlap by K rows above and below for the same
+// reason.  At the grid's own borders the mirror rule is applied either by
+// selects in the level loop or, for the single-grid FP32 kernel at K >= 4,
+// by loading the rows and columns beyond the border as mirror images.
 //
 // Per cell and level this does exactly what k_step1 does (same cell_update,
 // same rounding to the storage type), so K steps here equal K launches of
