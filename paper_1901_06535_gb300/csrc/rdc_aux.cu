@@ -197,28 +197,96 @@ __device__ __forceinline__ unsigned int chan(float x, float scale)
     return (unsigned int)__float2int_rn(__fmul_rn(255.0f, y));
 }
 
+// Four consecutive pixels of row i starting at column j0 (a multiple of 4):
+// u, v (or the timelapse record) and phi in vectors where the four lie inside
+// the grid, one 16-byte store when the output allows it.  HBM-bound: reads
+// the state and phi once, writes 4 bytes per pixel.
+// Four values from p (n of them inside the grid), widened to float; one
+// 16-byte (FP32) or 8-byte (16-bit) load when all four are inside.  Row
+// starts are 16-byte aligned for FP32 and 8-byte aligned for 16-bit storage
+// (the row pitch is a multiple of 16 bytes) and j0 is a multiple of 4.
+template <typename S>
+__device__ __forceinline__ void load4(const S* p, int n, float (&x)[4])
+{
+    if (n == 4) {
+        if constexpr (sizeof(S) == 4) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+            x[0] = q.x;
+            x[1] = q.y;
+            x[2] = q.z;
+            x[3] = q.w;
+            return;
+        } else if constexpr (sizeof(S) == 2) {
+            union {
+                uint2 d;
+                S h[4];
+            } q;
+            q.d = __ldg(reinterpret_cast<const uint2*>(p));
+#pragma unroll
+            for (int e = 0; e < 4; ++e) x[e] = (float)widen(q.h[e]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) x[e] = e < n ? (float)widen(p[e]) : 0.0f;
+}
+
+// phi values for the FP64 threshold test (exact for both phi types).
+template <typename P>
+__device__ __forceinline__ void load4_phi(const P* p, int n, double (&x)[4])
+{
+    if constexpr (sizeof(P) == 4) {
+        float f[4];
+        load4(p, n, f);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = (double)f[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = e < n ? (double)p[e] : 0.0;
+    }
+}
+
 template <typename S>
 __global__ void k_render(const S* __restrict__ u, const S* __restrict__ v,
                          const typename Traits<S>::PhiT* __restrict__ phi,
                          const float* __restrict__ tl, int W, int H, int64_t pitch,
                          int64_t tl_pitch, float u_scale, float v_scale, double thr,
-                         uchar4* __restrict__ out)
+                         uchar4* __restrict__ out, int vec_out)
 {
-    const int64_t n = (int64_t)W * H;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = k / W, j = k - i * W;
-        const int64_t o = i * pitch + j;
-        unsigned int r, b;
+    const int j0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (j0 >= W) return;
+    const int n = min(4, W - j0);
+    for (int i = blockIdx.y; i < H; i += gridDim.y) {
+        const int64_t o = (int64_t)i * pitch + j0;
+        float a[4], b[4];
+        double ph[4];
         if (tl) {  // timelapse: running maximum of u over the static substrate
-            r = chan(tl[i * tl_pitch + j], u_scale);
-            b = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                a[e] = e < n ? tl[(int64_t)i * tl_pitch + j0 + e] : 0.0f;
+                b[e] = 0.0f;
+            }
         } else {
-            r = chan((float)widen(u[o]), u_scale);
-            b = chan((float)widen(v[o]), v_scale);
+            load4(u + o, n, a);
+            load4(v + o, n, b);
         }
-        const unsigned int g = ((double)phi[o] >= thr) ? 255u : 0u;
-        out[k] = make_uchar4((unsigned char)r, (unsigned char)g, (unsigned char)b, 255);
+        load4_phi(phi + o, n, ph);
+        unsigned int px[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned int r = chan(a[e], u_scale);
+            const unsigned int bl = tl ? 0u : chan(b[e], v_scale);
+            const unsigned int g = (ph[e] >= thr) ? 255u : 0u;
+            px[e] = r | (g << 8) | (bl << 16) | (255u << 24);
+        }
+        uchar4* dst = out + (int64_t)i * W + j0;
+        if (vec_out && n == 4) {
+            *reinterpret_cast<uint4*>(dst) = make_uint4(px[0], px[1], px[2], px[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (e < n) *reinterpret_cast<unsigned int*>(dst + e) = px[e];
+        }
     }
 }
 
@@ -226,13 +294,16 @@ template <typename S>
 __global__ void k_timelapse(const S* __restrict__ u, float* __restrict__ tl, int W, int H,
                             int64_t pitch, int64_t tl_pitch, int reset)
 {
-    const int64_t n = (int64_t)W * H;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = k / W, j = k - i * W;
-        const float x = (float)widen(u[i * pitch + j]);
-        float* t = tl + i * tl_pitch + j;
-        *t = reset ? x : fmaxf(*t, x);
+    const int j0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (j0 >= W) return;
+    const int n = min(4, W - j0);
+    for (int i = blockIdx.y; i < H; i += gridDim.y) {
+        float x[4];
+        load4(u + (int64_t)i * pitch + j0, n, x);
+        float* t = tl + (int64_t)i * tl_pitch + j0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (e < n) t[e] = reset ? x[e] : fmaxf(t[e], x[e]);
     }
 }
 
@@ -435,14 +506,15 @@ cudaError_t launch_render(int prec, const void* u, const void* v, const void* ph
                           const float* tl, int W, int H, int64_t pitch, int64_t tl_pitch,
                           float u_scale, float v_scale, double thr, void* out, cudaStream_t st)
 {
-    const int t = 256;
-    const int b = grid_for((int64_t)W * H, t);
+    const int t = 128;
+    const dim3 grid((unsigned)(((W + 3) / 4 + t - 1) / t), (unsigned)min(H, 65535));
     uchar4* o = (uchar4*)out;
+    const int vec = ((uintptr_t)out % 16 == 0) && (W % 4 == 0);
     switch (prec) {
-        case P_F32: k_render<float><<<b, t, 0, st>>>((const float*)u, (const float*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
-        case P_F64: k_render<double><<<b, t, 0, st>>>((const double*)u, (const double*)v, (const double*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
-        case P_BF16: k_render<__nv_bfloat16><<<b, t, 0, st>>>((const __nv_bfloat16*)u, (const __nv_bfloat16*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
-        case P_F16: k_render<__half><<<b, t, 0, st>>>((const __half*)u, (const __half*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o); break;
+        case P_F32: k_render<float><<<grid, t, 0, st>>>((const float*)u, (const float*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
+        case P_F64: k_render<double><<<grid, t, 0, st>>>((const double*)u, (const double*)v, (const double*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
+        case P_BF16: k_render<__nv_bfloat16><<<grid, t, 0, st>>>((const __nv_bfloat16*)u, (const __nv_bfloat16*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
+        case P_F16: k_render<__half><<<grid, t, 0, st>>>((const __half*)u, (const __half*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -451,13 +523,13 @@ cudaError_t launch_render(int prec, const void* u, const void* v, const void* ph
 cudaError_t launch_timelapse(int prec, const void* u, float* tl, int W, int H, int64_t pitch,
                              int64_t tl_pitch, int reset, cudaStream_t st)
 {
-    const int t = 256;
-    const int b = grid_for((int64_t)W * H, t);
+    const int t = 128;
+    const dim3 grid((unsigned)(((W + 3) / 4 + t - 1) / t), (unsigned)min(H, 65535));
     switch (prec) {
-        case P_F32: k_timelapse<float><<<b, t, 0, st>>>((const float*)u, tl, W, H, pitch, tl_pitch, reset); break;
-        case P_F64: k_timelapse<double><<<b, t, 0, st>>>((const double*)u, tl, W, H, pitch, tl_pitch, reset); break;
-        case P_BF16: k_timelapse<__nv_bfloat16><<<b, t, 0, st>>>((const __nv_bfloat16*)u, tl, W, H, pitch, tl_pitch, reset); break;
-        case P_F16: k_timelapse<__half><<<b, t, 0, st>>>((const __half*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        case P_F32: k_timelapse<float><<<grid, t, 0, st>>>((const float*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        case P_F64: k_timelapse<double><<<grid, t, 0, st>>>((const double*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        case P_BF16: k_timelapse<__nv_bfloat16><<<grid, t, 0, st>>>((const __nv_bfloat16*)u, tl, W, H, pitch, tl_pitch, reset); break;
+        case P_F16: k_timelapse<__half><<<grid, t, 0, st>>>((const __half*)u, tl, W, H, pitch, tl_pitch, reset); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -73,6 +73,29 @@ def test_render_into_device_buffer(gpu):
         gpu.rdc_destroy(h)
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f64"])
+@pytest.mark.parametrize("W,H", [(1000, 600), (1001, 7), (3, 5)])
+def test_render_device_buffer_any_alignment(gpu, prec, W, H):
+    """The same bytes into a 16-byte aligned device buffer (vector stores
+    when W is a multiple of 4) and into one 4 bytes off (pixel stores), as
+    into host memory."""
+    import torch
+    p = gpu.rdc_params_default(precision=PREC[prec])
+    h = gpu.rdc_create(W, H, p)
+    try:
+        gpu.rdc_seed(h, W / 3, H / 2, max(1.0, min(W, H) / 4), 0.8)
+        gpu.rdc_step(h, 7)
+        host = gpu.rdc_render(h, gpu.RDC_RENDER_SNAPSHOT, 1.0, 3.0, 0.054)
+        raw = torch.zeros(H * W * 4 + 16, dtype=torch.uint8, device="cuda")
+        for off in (0, 4):
+            dev = raw[off:off + H * W * 4].view(H, W, 4)
+            gpu.rdc_render(h, gpu.RDC_RENDER_SNAPSHOT, 1.0, 3.0, 0.054, out=dev)
+            gpu.rdc_sync(h)
+            assert np.array_equal(dev.cpu().numpy(), host), off
+    finally:
+        gpu.rdc_destroy(h)
+
+
 LINES = [  # (x0, y0, x1, y1, width, value, snap)
     (10.0, 12.5, 120.0, 12.5, 2.0, 0.2, 0.0),
     (20.0, 30.0, 90.0, 80.0, 3.0, 0.0975, 15.0),
