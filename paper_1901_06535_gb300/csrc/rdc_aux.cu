@@ -1,6 +1,8 @@
 // Auxiliary kernels of librdc: rest-state initialisation, catalytic
 // stimulation (§2), the health flag, dtype conversion between packed host
 // order and the pitched device planes, and probe gathers.
+#include <cmath>
+
 #include "rdc_device.cuh"
 #include "rdc_internal.h"
 
@@ -231,18 +233,21 @@ __device__ __forceinline__ void load4(const S* p, int n, float (&x)[4])
     for (int e = 0; e < 4; ++e) x[e] = e < n ? (float)widen(p[e]) : 0.0f;
 }
 
-// phi values for the FP64 threshold test (exact for both phi types).
+// The green channel: phi >= thr compared in FP64.  For a float phi the
+// launcher passes thr_f, the smallest float >= thr, and phi >= thr_f in FP32
+// is the same test (GB300's FP64 pipe would otherwise bound the kernel).
 template <typename P>
-__device__ __forceinline__ void load4_phi(const P* p, int n, double (&x)[4])
+__device__ __forceinline__ void green4(const P* p, int n, double thr, float thr_f,
+                                       unsigned int (&g)[4])
 {
     if constexpr (sizeof(P) == 4) {
         float f[4];
         load4(p, n, f);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) x[e] = (double)f[e];
+        for (int e = 0; e < 4; ++e) g[e] = (f[e] >= thr_f) ? 255u : 0u;
     } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) x[e] = e < n ? (double)p[e] : 0.0;
+        for (int e = 0; e < 4; ++e) g[e] = (e < n && p[e] >= thr) ? 255u : 0u;
     }
 }
 
@@ -251,7 +256,7 @@ __global__ void k_render(const S* __restrict__ u, const S* __restrict__ v,
                          const typename Traits<S>::PhiT* __restrict__ phi,
                          const float* __restrict__ tl, int W, int H, int64_t pitch,
                          int64_t tl_pitch, float u_scale, float v_scale, double thr,
-                         uchar4* __restrict__ out, int vec_out)
+                         float thr_f, uchar4* __restrict__ out, int vec_out)
 {
     const int j0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (j0 >= W) return;
@@ -259,7 +264,7 @@ __global__ void k_render(const S* __restrict__ u, const S* __restrict__ v,
     for (int i = blockIdx.y; i < H; i += gridDim.y) {
         const int64_t o = (int64_t)i * pitch + j0;
         float a[4], b[4];
-        double ph[4];
+        unsigned int g[4];
         if (tl) {  // timelapse: running maximum of u over the static substrate
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -270,14 +275,13 @@ __global__ void k_render(const S* __restrict__ u, const S* __restrict__ v,
             load4(u + o, n, a);
             load4(v + o, n, b);
         }
-        load4_phi(phi + o, n, ph);
+        green4(phi + o, n, thr, thr_f, g);
         unsigned int px[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const unsigned int r = chan(a[e], u_scale);
             const unsigned int bl = tl ? 0u : chan(b[e], v_scale);
-            const unsigned int g = (ph[e] >= thr) ? 255u : 0u;
-            px[e] = r | (g << 8) | (bl << 16) | (255u << 24);
+            px[e] = r | (g[e] << 8) | (bl << 16) | (255u << 24);
         }
         uchar4* dst = out + (int64_t)i * W + j0;
         if (vec_out && n == 4) {
@@ -510,11 +514,14 @@ cudaError_t launch_render(int prec, const void* u, const void* v, const void* ph
     const dim3 grid((unsigned)(((W + 3) / 4 + t - 1) / t), (unsigned)min(H, 65535));
     uchar4* o = (uchar4*)out;
     const int vec = ((uintptr_t)out % 16 == 0) && (W % 4 == 0);
+    // smallest float >= thr (for float phi maps)
+    float thr_f = (float)thr;
+    if ((double)thr_f < thr) thr_f = std::nextafter(thr_f, INFINITY);
     switch (prec) {
-        case P_F32: k_render<float><<<grid, t, 0, st>>>((const float*)u, (const float*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
-        case P_F64: k_render<double><<<grid, t, 0, st>>>((const double*)u, (const double*)v, (const double*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
-        case P_BF16: k_render<__nv_bfloat16><<<grid, t, 0, st>>>((const __nv_bfloat16*)u, (const __nv_bfloat16*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
-        case P_F16: k_render<__half><<<grid, t, 0, st>>>((const __half*)u, (const __half*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, o, vec); break;
+        case P_F32: k_render<float><<<grid, t, 0, st>>>((const float*)u, (const float*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, thr_f, o, vec); break;
+        case P_F64: k_render<double><<<grid, t, 0, st>>>((const double*)u, (const double*)v, (const double*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, thr_f, o, vec); break;
+        case P_BF16: k_render<__nv_bfloat16><<<grid, t, 0, st>>>((const __nv_bfloat16*)u, (const __nv_bfloat16*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, thr_f, o, vec); break;
+        case P_F16: k_render<__half><<<grid, t, 0, st>>>((const __half*)u, (const __half*)v, (const float*)phi, tl, W, H, pitch, tl_pitch, u_scale, v_scale, thr, thr_f, o, vec); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -96,6 +96,31 @@ def test_render_device_buffer_any_alignment(gpu, prec, W, H):
         gpu.rdc_destroy(h)
 
 
+@pytest.mark.parametrize("thr", [0.1, float(np.float32(0.1)) + 1e-12, 0.125,
+                                 float(np.nextafter(np.float32(0.2), np.float32(0))),
+                                 -np.inf, np.inf, 1e300, 1e-300])
+def test_render_threshold_is_an_fp64_comparison(gpu, orc, thr):
+    """G = 255 exactly where phi >= thr in FP64, for float phi values on both
+    sides of thresholds that are and are not float values."""
+    W, H = 16, 4
+    f = np.float32
+    vals = [f(0.1), np.nextafter(f(0.1), f(0)), np.nextafter(f(0.1), f(1)), f(0.125),
+            np.nextafter(f(0.125), f(0)), f(0.2), np.nextafter(f(0.2), f(0)), f(0.054)]
+    phi = np.resize(np.array(vals, dtype=np.float32), (H, W))
+    p = gpu.rdc_params_default(precision=0)
+    h = gpu.rdc_create(W, H, p, phi)
+    try:
+        img = gpu.rdc_render(h, gpu.RDC_RENDER_SNAPSHOT, 1.0, 1.0, thr)
+        u = np.empty((H, W), dtype=np.float32)
+        v = np.empty((H, W), dtype=np.float32)
+        gpu.rdc_read(h, u, v)
+    finally:
+        gpu.rdc_destroy(h)
+    ref = orc.render(u, v, phi.astype(np.float64), 1.0, 1.0, thr=thr)
+    assert np.array_equal(img, ref)
+    assert np.array_equal(img[..., 1] == 255, phi.astype(np.float64) >= thr)
+
+
 LINES = [  # (x0, y0, x1, y1, width, value, snap)
     (10.0, 12.5, 120.0, 12.5, 2.0, 0.2, 0.0),
     (20.0, 30.0, 90.0, 80.0, 3.0, 0.0975, 15.0),
