@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "rdc.h"
@@ -334,16 +335,40 @@ static int upload_phi(rdc_sim* s, const void* phi_host, int dtype)
     return RDC_OK;
 }
 
-// Validates a host phi map and returns its maximum.
+// Validates every phi value and finds the largest; large maps are split
+// over host threads (each chunk is scanned in order, so the result does not
+// depend on the split).
 bool host_scan_phi(const void* phi_host, int dtype, int64_t n, const rdc_params* p,
-                  double* mx)
+                   double* mx)
 {
+    auto scan = [&](int64_t k0, int64_t k1, double* m_out) {
+        double m = -INFINITY;
+        for (int64_t k = k0; k < k1; ++k) {
+            const double x = dtype == 0 ? (double)((const float*)phi_host)[k]
+                                        : ((const double*)phi_host)[k];
+            if (!host_phi_ok(x, p)) return false;
+            if (x > m) m = x;
+        }
+        *m_out = m;
+        return true;
+    };
+    const int64_t kChunk = int64_t(1) << 22;
+    unsigned hw = std::thread::hardware_concurrency();
+    int nt = (int)std::min<int64_t>(std::min<unsigned>(hw ? hw : 1, 16u), (n + kChunk - 1) / kChunk);
+    if (nt <= 1) return scan(0, n, mx);
+    std::vector<double> part(nt, -INFINITY);
+    std::vector<char> ok(nt, 1);
+    std::vector<std::thread> th;
+    const int64_t per = (n + nt - 1) / nt;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t k0 = std::min(n, t * per), k1 = std::min(n, k0 + per);
+        th.emplace_back([&, t, k0, k1]() { ok[t] = scan(k0, k1, &part[t]) ? 1 : 0; });
+    }
+    for (auto& x : th) x.join();
     double m = -INFINITY;
-    for (int64_t k = 0; k < n; ++k) {
-        const double x = dtype == 0 ? (double)((const float*)phi_host)[k]
-                                    : ((const double*)phi_host)[k];
-        if (!host_phi_ok(x, p)) return false;
-        if (x > m) m = x;
+    for (int t = 0; t < nt; ++t) {
+        if (!ok[t]) return false;
+        m = std::max(m, part[t]);
     }
     *mx = m;
     return true;

@@ -64,15 +64,34 @@ __global__ void k_rest(S* __restrict__ u, S* __restrict__ v,
                        const typename Traits<S>::PhiT* __restrict__ phi, int W,
                        int H, int64_t pitch, double f, double q)
 {
+    // Each thread keeps the last phi it met and that phi's root; a warp runs
+    // the bisection only when one of its lanes meets a new value (phi maps
+    // are piecewise constant, so most warps skip it).  The loop keeps whole
+    // warps together so the vote covers every lane.
     const int64_t n = (int64_t)W * H;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = k / W, j = k - i * W;
-        const int64_t o = i * pitch + j;
-        const double r = rest_root((double)phi[o], f, q);
-        const S s = cvt_from_double<S>(r);
-        u[o] = s;
-        v[o] = s;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    double last_phi = NAN, last_root = 0.0;
+    for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < n;
+         k0 += stride) {
+        const int64_t k = k0 + (threadIdx.x & 31);
+        const bool live = k < n;
+        int64_t o = 0;
+        double ph = last_phi;
+        if (live) {
+            const int64_t i = k / W, j = k - i * W;
+            o = i * pitch + j;
+            ph = (double)phi[o];
+        }
+        const bool need = live && !(ph == last_phi);
+        if (__any_sync(0xffffffffu, need) && need) {
+            last_root = rest_root(ph, f, q);
+            last_phi = ph;
+        }
+        if (live) {
+            const S s = cvt_from_double<S>(last_root);
+            u[o] = s;
+            v[o] = s;
+        }
     }
 }
 

@@ -153,3 +153,17 @@ def test_stoch_round_sample_validates_before_touching_the_device(librdc):
 def test_params_reject_unknown_fields(librdc):
     with pytest.raises(TypeError):
         librdc.rdc_params_default(reserved=0)
+
+
+def test_large_phi_map_validation_is_threaded_and_exact(librdc):
+    """Maps larger than one scan chunk (2^22 cells) are validated on several
+    host threads: an invalid value anywhere is still refused (before any
+    device call), in every chunk position."""
+    W, H = 4096, 3000                  # 12.3 M cells: several chunks
+    p = librdc.rdc_params_default()
+    for pos in (0, 5_000_000, W * H - 1):
+        phi = np.full((H, W), 0.054, dtype=np.float32)
+        phi.flat[pos] = np.nan if pos % 2 else 0.001
+        with pytest.raises(librdc.RdcError) as e:
+            librdc.rdc_create(W, H, p, phi)
+        assert e.value.status == librdc.RDC_EINVAL, pos
