@@ -593,6 +593,7 @@ int rdc_step(rdc_sim* s, int64_t n)
         cudaError_t e;
         int done;
         m.step0 = s->steps_done;  // index of the state this launch reads
+        m.flip = (int)(s->launches & 1);  // alternate the single step's sweep direction
         if (k > 1 && left >= k) {
             e = launch_kblock(s->prec, s->mode, g, m, s->shapek, s->stream);
             done = k;

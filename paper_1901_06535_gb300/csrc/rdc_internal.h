@@ -15,6 +15,7 @@ struct ModelD {
     int sr = 0;           // 1: stochastic rounding to the 16-bit storage type
     unsigned seed = 0;    // key of the rounding stream
     long long step0 = 0;  // index of the state a launch reads; level l writes step0 + l
+    int flip = 0;         // single-step kernel: row blocks in reverse order
 };
 
 // Which terms of u_t a step evaluates (match the RDC_*_ONLY flags), plus
