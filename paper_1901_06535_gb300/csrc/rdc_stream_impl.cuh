@@ -154,31 +154,48 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
 #pragma unroll
         for (int e = 0; e < N; ++e)
             P0[l][e] = P1[l][e] = P2[l][e] = Q0[l][e] = Q1[l][e] = F[l][e] = T(0);
-    // For K >= 3, row t's u, v and phi are loaded one iteration ahead of their
-    // first use (level 1 needs row t at once, and rows stream from HBM):
-    // measured +25 % at K = 3 and +11 % at K = 6 (8192^2, FP32), -14 % at K = 2,
-    // whose four cells per lane leave no registers for the extra row.
-    constexpr bool AHEAD = K >= 3;
-    T pu[N], pv[N], pp[N];
+    // Row t's u, v and phi are loaded DIST iterations ahead of their first use
+    // (level 1 needs row t at once, and rows stream from HBM).  Measured at
+    // 8192^2: one row ahead +25 % at K = 3 and +11 % at K = 6 (FP32); two rows
+    // ahead another +6 % for the single-grid FP32 kernel at K >= 5 (GH), but
+    // -9 % with 16-bit storage and -4 % in the batched kernel; none at K = 2,
+    // whose four cells per lane leave no registers (-14 %).
+    constexpr int DIST = (GH && K >= 5) ? 2 : (K >= 3 ? 1 : 0);
+    T pu[N], pv[N], pp[N], qu[N], qv[N], qp[N];
 #pragma unroll
-    for (int e = 0; e < N; ++e) pu[e] = pv[e] = pp[e] = T(0);
-    if (AHEAD) load_row(t0, pu, pv, pp);
-    constexpr int UNROLL = (K >= 4) ? 3 : 1;
+    for (int e = 0; e < N; ++e) pu[e] = pv[e] = pp[e] = qu[e] = qv[e] = qp[e] = T(0);
+    if (DIST >= 1) load_row(t0, pu, pv, pp);
+    if (DIST >= 2 && t0 + 1 <= t_end) load_row(t0 + 1, qu, qv, qp);
+    // Unrolled row loop: the three-row rotation becomes renaming; the
+    // single-grid FP32 kernel at K = 4 (GH) runs best unrolled six times
+    // (835 vs 813 G cell-updates/s; six times lost 17 % with 16-bit storage
+    // and 3 % in the batched kernel).
+    constexpr int UNROLL = (GH && K == 4) ? 6 : ((K >= 4) ? 3 : 1);
 #pragma unroll UNROLL
     for (int t = t0; t <= t_end; ++t) {
         T nphi[N];
         {
             T nu[N], nv[N];
-            const int tl = AHEAD ? t + 1 : t;  // the row loaded in this iteration
 #pragma unroll
             for (int e = 0; e < N; ++e) {
                 nu[e] = pu[e];
                 nv[e] = pv[e];
                 nphi[e] = pp[e];
-                pu[e] = pv[e] = pp[e] = T(0);
+                if (DIST == 2) {
+                    pu[e] = qu[e];
+                    pv[e] = qv[e];
+                    pp[e] = qp[e];
+                    qu[e] = qv[e] = qp[e] = T(0);
+                } else {
+                    pu[e] = pv[e] = pp[e] = T(0);
+                }
             }
-            if (tl <= t_end) load_row(tl, pu, pv, pp);
-            if constexpr (!AHEAD) {
+            const int tl = t + DIST;  // the row loaded in this iteration
+            if (tl <= t_end) {
+                if (DIST == 2) load_row(tl, qu, qv, qp);
+                else load_row(tl, pu, pv, pp);
+            }
+            if constexpr (DIST == 0) {
 #pragma unroll
                 for (int e = 0; e < N; ++e) {
                     nu[e] = pu[e];
@@ -301,10 +318,12 @@ __device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __
     stream_warp_impl<S, MODE, K, N, GH>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
 }
 
-// Mirrored ghost cells instead of border selects: measured faster for the
-// single-grid FP32 kernel at K >= 4 (K = 4: 724 -> 805, K = 6: 760 -> 786 G
-// cell-updates/s at 8192^2), slower for K <= 3, 16-bit storage and the
-// batched kernel, whose register budgets it exceeds.
+// The single-grid FP32 kernel at K >= 4 (GH) takes the variants that
+// measured faster there: mirrored ghost cells instead of border selects
+// (K = 4: 724 -> 805, K = 6: 760 -> 786 G cell-updates/s at 8192^2), rows
+// two iterations ahead at K >= 5 and a six-fold unroll at K = 4; they were
+// slower for K <= 3, 16-bit storage and the batched kernel, whose register
+// budgets they exceed.
 template <typename S, int K>
 constexpr bool stream_ghost() { return sizeof(S) == 4 && K >= 4; }
 
