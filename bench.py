@@ -491,7 +491,7 @@ def _serving(pkg, frames=100, steps_per_frame=50):
     specs = ri.diode_sessions(seed=5, n=64, frames=frames)
     sessions = [serve.Session(s.sid, s.size, s.size, phi=s.phi, frames=frames,
                               touches=s.touches) for s in specs]
-    srv = serve.Server(precision=0, k_block=4, steps_per_frame=steps_per_frame)
+    srv = serve.Server(precision=0, k_block=6, steps_per_frame=steps_per_frame)
     try:
         wall, st = serve.run_workload(sessions, [s.arrival for s in specs], srv)
     finally:
