@@ -85,17 +85,17 @@ struct StreamGeom {
 // launch (k_stepk_stream) and a work list over many grids (k_stream_batch).
 //
 // The row loop's body is straight-line code: every level computes its row
-// even when that row lies outside the grid, and the mirror borders are
-// applied by selects.  Rows outside the grid hold garbage that no valid cell
-// ever reads: the select at rows 0 and H-1 (and columns 0 and W-1) replaces
-// the out-of-range neighbour by the cell itself.  phi of row t is loaded
-// with row t's u and v and handed down the levels in a K-deep register queue
-// (level l at iteration t needs row t - l), so each row's phi is read once
-// and one iteration before its first use; reloading it at every level made
-// load latency the main stall.  Straight-line code lets the compiler interleave the
-// levels' arithmetic; warp-uniform branches there measured slower.  For
-// K >= 4 the row loop is unrolled three times, which turns the three-row
-// register rotation into renaming.
+// even when that row lies outside the grid (garbage that no valid cell ever
+// reads).  The mirror borders are applied either by selects (the select at
+// rows 0 and H-1 and columns 0 and W-1 replaces the out-of-range neighbour by
+// the cell itself) or, with GHOST, by loading the rows and columns beyond the
+// border as mirror images.  phi of row t is loaded with row t's u and v and
+// handed down the levels in a K-deep register queue (level l at iteration t
+// needs row t - l), so each row's phi is read once; rows are loaded DIST
+// iterations before their first use.  Straight-line code lets the compiler
+// interleave the levels' arithmetic (warp-uniform branches in the level loop
+// measured slower); the row loop is unrolled so that the three-row register
+// rotation becomes renaming.
 template <typename S, int MODE, int K, int N, bool GH>
 __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                                                  const S* __restrict__ v,
@@ -164,8 +164,9 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     T pu[N], pv[N], pp[N], qu[N], qv[N], qp[N];
 #pragma unroll
     for (int e = 0; e < N; ++e) pu[e] = pv[e] = pp[e] = qu[e] = qv[e] = qp[e] = T(0);
-    if (DIST >= 1) load_row(t0, pu, pv, pp);
-    if (DIST >= 2 && t0 + 1 <= t_end) load_row(t0 + 1, qu, qv, qp);
+    if constexpr (DIST >= 1) load_row(t0, pu, pv, pp);
+    if constexpr (DIST >= 2)
+        if (t0 + 1 <= t_end) load_row(t0 + 1, qu, qv, qp);
     // Unrolled row loop: the three-row rotation becomes renaming; the
     // single-grid FP32 kernel at K = 4 (GH) runs best unrolled six times
     // (835 vs 813 G cell-updates/s; six times lost 17 % with 16-bit storage
@@ -181,7 +182,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                 nu[e] = pu[e];
                 nv[e] = pv[e];
                 nphi[e] = pp[e];
-                if (DIST == 2) {
+                if constexpr (DIST == 2) {
                     pu[e] = qu[e];
                     pv[e] = qv[e];
                     pp[e] = qp[e];
@@ -192,7 +193,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
             }
             const int tl = t + DIST;  // the row loaded in this iteration
             if (tl <= t_end) {
-                if (DIST == 2) load_row(tl, qu, qv, qp);
+                if constexpr (DIST == 2) load_row(tl, qu, qv, qp);
                 else load_row(tl, pu, pv, pp);
             }
             if constexpr (DIST == 0) {
