@@ -8,7 +8,9 @@
 //            the north / centre / south rows of u in registers, so u is read
 //            from memory once; east/west neighbours across vector edges come
 //            from warp shuffles, and only the two cells beyond each warp's
-//            span are loaded separately.
+//            span are loaded separately.  FP32-compute cells go in pairs
+//            (cell_update2); consecutive launches alternate the row order so
+//            each step starts on rows still in L2.
 //  k_stepk : k Euler steps per launch (temporal blocking).  A CTA loads a
 //            (tx + 2k) x (ty + 2k) tile of u, v, phi into shared memory and
 //            steps it k times, the valid region shrinking by one cell per
