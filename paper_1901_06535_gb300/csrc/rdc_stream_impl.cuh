@@ -63,6 +63,21 @@ struct VecN {
     }
 };
 
+// Two values through the 16-bit storage type and back, one paired
+// conversion each way (round to nearest even per value, as quantize).
+template <typename S>
+__device__ __forceinline__ float2 quantize2(float2 x);
+template <>
+__device__ __forceinline__ float2 quantize2<__nv_bfloat16>(float2 x)
+{
+    return __bfloat1622float2(__float22bfloat162_rn(x));
+}
+template <>
+__device__ __forceinline__ float2 quantize2<__half>(float2 x)
+{
+    return __half22float2(__float22half2_rn(x));
+}
+
 // Mirror image of index x in [0, n) under the cell-centred zero-flux
 // border: -1 -> 0, -2 -> 1, n -> n - 1, ... (repeated for grids narrower
 // than the reach).
@@ -255,6 +270,12 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                             nu[e + 1] = quantize_sr<S>(un.y, w1);
                             nv[e] = quantize_sr<S>(vn.x, w0 << 16);
                             nv[e + 1] = quantize_sr<S>(vn.y, w1 << 16);
+                        } else if constexpr (sizeof(S) == 2) {
+                            const float2 qu = quantize2<S>(un), qv = quantize2<S>(vn);
+                            nu[e] = qu.x;
+                            nu[e + 1] = qu.y;
+                            nv[e] = qv.x;
+                            nv[e + 1] = qv.y;
                         } else {
                             nu[e] = quantize<S>(un.x);
                             nu[e + 1] = quantize<S>(un.y);
