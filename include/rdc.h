@@ -190,6 +190,16 @@ int rdc_set_phi(rdc_sim* sim, const void* phi_host, int32_t dtype);
 int rdc_reset_rest(rdc_sim* sim);
 
 /*
+ * Sets the step index (steps_done of rdc_view): the index of the current
+ * state, from which RDC_STOCH_ROUND derives its random stream.  To resume a
+ * stochastically rounded run from a checkpoint bit for bit, restore the
+ * state with rdc_set_state and the index saved with it (rdc_get_view's
+ * steps_done) here.  Round-to-nearest modes do not depend on it.
+ * RDC_EINVAL: sim NULL or n < 0.
+ */
+int rdc_set_step_index(rdc_sim* sim, int64_t n);
+
+/*
  * Async.  Catalytic stimulation (§2): u := value (rounded to the storage
  * type) for every cell (i, j) with (i - cy)^2 + (j - cx)^2 <= r^2, the
  * squares and the sum taken in FP64 round-to-nearest with no contraction;
@@ -498,6 +508,10 @@ void rdc_batch_destroy(rdc_batch* b);
 
 /* Async.  Stimulation of grid idx, as rdc_seed. */
 int rdc_batch_seed(rdc_batch* b, int32_t idx, double cx, double cy, double r, double value);
+
+/* Sets grid idx's step index, as rdc_set_step_index (for resuming a
+ * stochastically rounded grid from a checkpoint). */
+int rdc_batch_set_step_index(rdc_batch* b, int32_t idx, int64_t n);
 
 /* Sets grid idx's current state from packed host arrays, as rdc_set_state. */
 int rdc_batch_set_state(rdc_batch* b, int32_t idx, const void* u_host, const void* v_host,

@@ -122,6 +122,7 @@ _SIGS = {
     "rdc_destroy": (None, [_P]),
     "rdc_set_phi": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "rdc_reset_rest": (ctypes.c_int, [_P]),
+    "rdc_set_step_index": (ctypes.c_int, [_P, ctypes.c_int64]),
     "rdc_seed": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "rdc_set_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     "rdc_step": (ctypes.c_int, [_P, ctypes.c_int64]),
@@ -147,6 +148,7 @@ _SIGS = {
     "rdc_batch_seed": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double]),
     "rdc_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
+    "rdc_batch_set_step_index": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
     "rdc_batch_step": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int64]),
     "rdc_batch_check": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "rdc_batch_read": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32]),
@@ -328,6 +330,14 @@ def rdc_set_phi(h, phi) -> int:
 
 def rdc_reset_rest(h) -> int:
     return _chk(lib().rdc_reset_rest(h), "rdc_reset_rest")
+
+
+def rdc_set_step_index(h, n: int) -> int:
+    return _chk(lib().rdc_set_step_index(h, int(n)), "rdc_set_step_index")
+
+
+def rdc_batch_set_step_index(b, idx: int, n: int) -> int:
+    return _chk(lib().rdc_batch_set_step_index(b, int(idx), int(n)), "rdc_batch_set_step_index")
 
 
 def rdc_seed(h, cx: float, cy: float, r: float, value: float) -> int:

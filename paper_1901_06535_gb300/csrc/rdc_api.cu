@@ -535,6 +535,13 @@ int rdc_reset_rest(rdc_sim* s)
     return RDC_OK;
 }
 
+int rdc_set_step_index(rdc_sim* s, int64_t n)
+{
+    if (!s || n < 0) return RDC_EINVAL;
+    s->steps_done = n;
+    return RDC_OK;
+}
+
 int rdc_set_phi(rdc_sim* s, const void* phi_host, int32_t dtype)
 {
     if (!s || !phi_host || (dtype != 0 && dtype != 1)) return RDC_EINVAL;

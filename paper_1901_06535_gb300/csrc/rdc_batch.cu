@@ -437,6 +437,13 @@ int rdc_batch_set_state(rdc_batch* b, int32_t idx, const void* u_host, const voi
     return RDC_OK;
 }
 
+int rdc_batch_set_step_index(rdc_batch* b, int32_t idx, int64_t n)
+{
+    if (!b || idx < 0 || idx >= b->n || !b->mem[idx] || n < 0) return RDC_EINVAL;
+    b->desc[idx].steps = n;  // uploaded with the descriptors at the next step
+    return RDC_OK;
+}
+
 int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n)
 {
     if (!b || n < 0) return RDC_EINVAL;

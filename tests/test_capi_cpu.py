@@ -167,3 +167,10 @@ def test_large_phi_map_validation_is_threaded_and_exact(librdc):
         with pytest.raises(librdc.RdcError) as e:
             librdc.rdc_create(W, H, p, phi)
         assert e.value.status == librdc.RDC_EINVAL, pos
+
+
+def test_set_step_index_validates(librdc):
+    import ctypes
+    L = librdc.lib()
+    assert L.rdc_set_step_index(None, 5) == librdc.RDC_EINVAL
+    assert L.rdc_batch_set_step_index(None, 0, 5) == librdc.RDC_EINVAL
