@@ -174,3 +174,18 @@ def test_set_step_index_validates(librdc):
     L = librdc.lib()
     assert L.rdc_set_step_index(None, 5) == librdc.RDC_EINVAL
     assert L.rdc_batch_set_step_index(None, 0, 5) == librdc.RDC_EINVAL
+
+
+def test_noalloc_refuses_stochastic_rounding(librdc):
+    """rdc_step_noalloc keeps no step index across calls, so it refuses
+    RDC_STOCH_ROUND (before any device call)."""
+    import ctypes
+    L = librdc.lib()
+    p = librdc.rdc_params_default(precision=2, flags=librdc.RDC_STOCH_ROUND, round_seed=1)
+    fake = 1 << 40
+    bad = ctypes.c_int64(0)
+    from paper_1901_06535_gb300._capi import rdc_grid
+    rc = L.rdc_step_noalloc(rdc_grid(16, 16), ctypes.byref(p), fake, fake + 4096,
+                            fake + 8192, fake + 12288, fake + 16384, 64, 3, None,
+                            ctypes.byref(bad))
+    assert rc == librdc.RDC_EINVAL

@@ -154,3 +154,26 @@ def test_arrival_times_c1_stochastic(gpu, orc, om, prec, record_property):
     record_property("arrival_rel_err", rel.tolist())
     print(f"[{prec} SR] arrival times {t.tolist()} vs oracle {t_ref.tolist()}: rel {rel.tolist()}")
     assert np.all(rel <= 0.01), (prec, t_ref, t, rel)
+
+
+def test_tuning_keeps_the_stochastic_bits(gpu):
+    """rdc_tune times candidate shapes on the spare buffers: the state, the
+    step index and hence the random stream are unchanged, and the tuned
+    shape gives the bits of single steps."""
+    W, H, n = 260, 190, 21
+    s = _seeds(W, H)
+    ref, _, _ = gpu_run(gpu, W, H, seeds=s, n=n, prec="bf16", flags=SR, round_seed=4, k=1)
+    p = gpu.rdc_params_default(precision=PREC["bf16"], flags=SR, round_seed=4)
+    h = gpu.rdc_create(W, H, p)
+    try:
+        for d in s:
+            gpu.rdc_seed(h, *d)
+        gpu.rdc_step(h, 5)
+        gpu.rdc_tune(h, 2)
+        assert gpu.rdc_get_view(h).steps_done == 5
+        gpu.rdc_step(h, n - 5)
+        u = np.empty((H, W))
+        gpu.rdc_read(h, u, None)
+    finally:
+        gpu.rdc_destroy(h)
+    assert np.array_equal(u, ref)
