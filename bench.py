@@ -38,6 +38,7 @@ EULER_STEPS = 10000
 N_DISKS = 200
 DISK_SEED = 3
 BYTES_PER_CELL = {"f32": 20, "bf16": 12, "f16": 12, "f64": 40}
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth
 STORAGE_TYPE = {"f32": "float", "f64": "double", "bf16": "__nv_bfloat16", "f16": "__half"}
 METRIC = "GCUPS (cell-updates/s)"
 
@@ -360,6 +361,8 @@ def main():
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": peak_kind,
+                             "nominal_peak": NOMINAL_HBM_GBS,
+                             "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                              "traffic": (_traffic("k_step1<float>", W * H)
                                          if args.kblock == 1 and args.precision == "f32" else None),
                              "kernel": f"{'k_step1' if args.kblock == 1 else 'k_stepk_stream'}"
