@@ -88,3 +88,22 @@ def test_c2_stochastic_rounding_truth_table(gpu, prec, record_property):
     print(f"{prec} + stochastic rounding AND truth tables at 1024^2:", tables)
     for seed, t in tables.items():
         assert t == {"-": False, "A": False, "B": False, "AB": True}, (seed, t)
+
+
+def test_c2_maxabs_1000_reported(gpu, record_property):
+    """Pointwise max-abs of u against FP64 after 1000 steps of the C2 workload
+    (both inputs fired), for each reduced mode: reported, with a sanity
+    bound.  FP64 on the GPU is the oracle's result bit for bit (tested
+    elsewhere), so it stands in for the oracle at this size."""
+    c = _circuit()
+    seeds = [(*c.seeds["A"], 0.8), (*c.seeds["B"], 0.8)]
+    ref, _, _ = gpu_run(gpu, N, N, phi=c.phi, seeds=seeds, n=1000, prec="f64", k=1)
+    out = {}
+    for name, prec, flags in (("f32", "f32", 0), ("f16", "f16", 0), ("bf16", "bf16", 0),
+                              ("bf16_stoch", "bf16", 4), ("f16_stoch", "f16", 4)):
+        u, _, _ = gpu_run(gpu, N, N, phi=c.phi.astype(np.float32), seeds=seeds, n=1000,
+                          prec=prec, k=4, flags=flags, round_seed=1 if flags else 0)
+        out[name] = float(np.max(np.abs(u - ref)))
+    record_property("c2_maxabs_u_1000", out)
+    print("C2 max-abs of u vs FP64 after 1000 steps:", {k: f"{v:.2e}" for k, v in out.items()})
+    assert out["f32"] < 0.05 and all(v < 0.9 for v in out.values())
