@@ -5,7 +5,9 @@
    neighbour, exchanged every step (v and phi are local: v does not diffuse,
    Eq. 1, and phi is static).  The gathered result must equal the unsplit
    oracle bit for bit -- the exchange a multi-GPU strip path would need.
-2. The benchmark's rank aggregation: the slowest rank's time and the
+2. The same with temporal blocking: K rows of u and v every K steps, the
+   halo recomputed (K = 4, 6).
+3. The benchmark's rank aggregation: the slowest rank's time and the
    whole-job (weak-scaling) rate.
 """
 from __future__ import annotations
@@ -94,6 +96,74 @@ def test_row_strips_with_halo_exchange_equal_unsplit(tmp_path):
     out = str(tmp_path / "strips.npz")
     mp.start_processes(_strip_worker, args=(2, _free_port(), out), nprocs=2, join=True,
                        start_method="spawn")
+    orc, phi, u, v = _initial()
+    ref = orc.run(phi, u, v, STEPS)
+    got = np.load(out)
+    assert np.array_equal(got["u"], ref["u"]) and np.array_equal(got["v"], ref["v"])
+
+
+def _kblock_strip_worker(rank, world, port, out_path, K):
+    """Temporally blocked strips: every K steps each rank exchanges K rows of
+    u and v with each neighbour and steps its strip, extended by those halo
+    rows, K times; the halo's cut edge corrupts one row per step, so after K
+    steps exactly the owned rows are still exact (ghost-zone recompute)."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    orc, phi, u, v = _initial()
+    bounds = np.linspace(0, H, world + 1).astype(int)
+    r0, r1 = bounds[rank], bounds[rank + 1]
+    up, dn = rank > 0, rank < world - 1
+    us, vs = u[r0:r1].copy(), v[r0:r1].copy()
+    e0, e1 = (r0 - K if up else r0), (r1 + K if dn else r1)
+    ph = phi[e0:e1]
+    assert STEPS % K == 0
+    for _ in range(STEPS // K):
+        got = {}
+        reqs = []
+        for name, nb, rows in (("top", rank - 1, slice(0, K)), ("bot", rank + 1, slice(-K, None))):
+            if (name == "top" and not up) or (name == "bot" and not dn):
+                continue
+            for arr, key in ((us, "u"), (vs, "v")):
+                reqs.append(dist.isend(torch.from_numpy(arr[rows].ravel().copy()), nb))
+                buf = torch.empty(K * W, dtype=torch.float64)
+                reqs.append(dist.irecv(buf, nb))
+                got[(name, key)] = buf
+        for q in reqs:
+            q.wait()
+        def ext(a, key):
+            parts = ([got[("top", key)].numpy().reshape(K, W)] if up else []) + [a] + \
+                    ([got[("bot", key)].numpy().reshape(K, W)] if dn else [])
+            return np.ascontiguousarray(np.concatenate(parts))
+        out = orc.run(np.ascontiguousarray(ph), ext(us, "u"), ext(vs, "v"), K)
+        a = K if up else 0
+        us = out["u"][a:a + (r1 - r0)].copy()
+        vs = out["v"][a:a + (r1 - r0)].copy()
+    if rank == 0:
+        parts_u, parts_v = [us], [vs]
+        for src in range(1, world):
+            n = (bounds[src + 1] - bounds[src]) * W
+            tu = torch.empty(n, dtype=torch.float64)
+            tv = torch.empty(n, dtype=torch.float64)
+            dist.recv(tu, src)
+            dist.recv(tv, src)
+            parts_u.append(tu.numpy().reshape(-1, W))
+            parts_v.append(tv.numpy().reshape(-1, W))
+        np.savez(out_path, u=np.concatenate(parts_u), v=np.concatenate(parts_v))
+    else:
+        dist.send(torch.from_numpy(us.ravel().copy()), 0)
+        dist.send(torch.from_numpy(vs.ravel().copy()), 0)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("K", [4, 6])
+def test_kblocked_strips_equal_unsplit(tmp_path, K):
+    """K rows of u and v every K steps suffice (the temporally blocked form of
+    the strip exchange); the result equals the unsplit oracle bit for bit."""
+    out = str(tmp_path / f"kstrips{K}.npz")
+    mp.start_processes(_kblock_strip_worker, args=(2, _free_port(), out, K), nprocs=2,
+                       join=True, start_method="spawn")
     orc, phi, u, v = _initial()
     ref = orc.run(phi, u, v, STEPS)
     got = np.load(out)
