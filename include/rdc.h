@@ -368,11 +368,13 @@ typedef struct {
     int32_t width, height;
     int32_t precision;
     int32_t elem_bytes;   /* bytes per stored u or v value */
-    int64_t steps_done;   /* Euler steps applied since create / reset */
+    int64_t steps_done;   /* step index: Euler steps applied since create / reset
+                             (or as set by rdc_set_step_index) */
     int64_t launches;     /* step-kernel launches enqueued so far */
     void* stream;         /* the simulation's cudaStream_t */
 } rdc_view;
 
+/* Fills *out (see rdc_view).  RDC_EINVAL if sim or out is NULL. */
 int rdc_get_view(rdc_sim* sim, rdc_view* out);
 
 /* Launch shapes of the step kernels.  They change speed only: results are
@@ -540,6 +542,8 @@ int rdc_batch_sync(rdc_batch* b);
  * valid configuration gives the same bits. */
 int rdc_batch_set_config(rdc_batch* b, int32_t k, int32_t rows, int32_t krows, int32_t graphs);
 
+/* Fills *out with the batch's configuration and counters (rdc_batch_info).
+ * RDC_EINVAL if b or out is NULL. */
 int rdc_batch_get_info(rdc_batch* b, rdc_batch_info* out);
 
 /*
