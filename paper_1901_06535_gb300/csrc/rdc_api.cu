@@ -285,6 +285,8 @@ static void default_shapes(rdc_sim* s)
     int krows = s->shapek.k >= 5 ? 128 : 64;
     while (krows > 16 && (int64_t)((s->W + 111) / 112) * ((s->H + krows - 1) / krows) < 152 * 16)
         krows /= 2;
+    // and few enough CTA rows for the 65535 limit of gridDim.y on tall grids
+    while ((s->H + krows - 1) / krows > 65535) krows *= 2;
     s->shapek.krows = krows;
 }
 

@@ -55,3 +55,38 @@ def test_beyond_2_pow_31_cells(gpu, orc, om, k):
     want = ref[ii - i0, jj - j0]
     assert np.max(np.abs(got - want)) < 4e-6
     assert np.max(got) > 0.5                     # the stimulated disk is there
+
+
+def test_tall_grid_default_shape(gpu, orc, om):
+    """A grid taller than 65535 x 64 rows (64 x 4,200,000): the default
+    launch shapes (k = 4 streamed steps) keep gridDim.y within its 65535
+    limit, and the cells near the bottom border match the oracle."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 8 * 2**30:
+        pytest.skip("needs about 6 GB of free device memory")
+    w, h_rows, n = 64, 4_200_000, 8
+    seed = (40.0, h_rows - 12.0, 6.0, 0.8)
+    p = gpu.rdc_params_default(precision=0)
+    h = gpu.rdc_create(w, h_rows, p)
+    try:
+        s = gpu.rdc_get_shape(h)
+        assert s.k == 4 and s.variant == 0
+        assert (h_rows + s.krows - 1) // s.krows <= 65535
+        gpu.rdc_seed(h, *seed)
+        gpu.rdc_step(h, n)
+        assert gpu.rdc_check(h) == (0, -1)
+        rows = np.arange(h_rows - PROBE_ROWS, h_rows)
+        ii, jj = np.meshgrid(rows, np.arange(w), indexing="ij")
+        got = gpu.rdc_probe(h, (ii.astype(np.int64) * w + jj).ravel()).reshape(ii.shape)
+    finally:
+        gpu.rdc_destroy(h)
+    # oracle on the bottom rows: the window's top edge (a cut, not a border)
+    # lies n + 2 rows above the probed block
+    i0 = h_rows - PROBE_ROWS - (n + 2)
+    phi = np.full((h_rows - i0, w), 0.054)
+    u, v = orc.rest_field(phi)
+    orc.seed_disk(u, seed[0], seed[1] - i0, seed[2], seed[3])
+    ref = orc.run(phi, u, v, n)["u"]
+    assert np.max(np.abs(got - ref[ii - i0, jj])) < 4e-6
+    assert np.max(got) > 0.5
