@@ -933,6 +933,10 @@ int rdc_tune(rdc_sim* s, int32_t reps, rdc_launch_shape* out, double* best_gcups
     for (const Cand& c : cands) {
         const bool use_k = c.kblock;
         if (use_k && c.sk.variant == 1 && stepk_smem_bytes(s->prec, c.sk) > 227 * 1024) continue;
+        // shapes whose CTA rows exceed gridDim.y's 65535 on a tall grid
+        if (use_k && (s->H + (c.sk.variant == 0 ? c.sk.krows : c.sk.ty) - 1) /
+                             (c.sk.variant == 0 ? c.sk.krows : c.sk.ty) > 65535)
+            continue;
         // each timed launch reads the current buffers and writes the spare ones
         auto launch = [&]() {
             return use_k ? launch_kblock(s->prec, s->mode, g, m, c.sk, s->stream)

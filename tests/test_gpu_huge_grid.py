@@ -59,8 +59,9 @@ def test_beyond_2_pow_31_cells(gpu, orc, om, k):
 
 def test_tall_grid_default_shape(gpu, orc, om):
     """A grid taller than 65535 x 64 rows (64 x 4,200,000): the default
-    launch shapes (k = 4 streamed steps) keep gridDim.y within its 65535
-    limit, and the cells near the bottom border match the oracle."""
+    launch shapes (k = 4 streamed steps) and the autotuner's candidates keep
+    gridDim.y within its 65535 limit, and the cells near the bottom border
+    match the oracle."""
     import torch
     free, _ = torch.cuda.mem_get_info()
     if free < 8 * 2**30:
@@ -76,6 +77,13 @@ def test_tall_grid_default_shape(gpu, orc, om):
         gpu.rdc_seed(h, *seed)
         gpu.rdc_step(h, n)
         assert gpu.rdc_check(h) == (0, -1)
+        # the autotuner skips the shapes that would exceed the limit; its
+        # timing launches leave the current state alone
+        t, gcups = gpu.rdc_tune(h, reps=1)
+        assert gcups > 0
+        if t["k"] > 1:
+            rows_per_cta = t["krows"] if t["variant"] == 0 else t["ty"]
+            assert (h_rows + rows_per_cta - 1) // rows_per_cta <= 65535, t
         rows = np.arange(h_rows - PROBE_ROWS, h_rows)
         ii, jj = np.meshgrid(rows, np.arange(w), indexing="ij")
         got = gpu.rdc_probe(h, (ii.astype(np.int64) * w + jj).ravel()).reshape(ii.shape)
