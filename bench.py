@@ -252,6 +252,13 @@ def main():
                     help="storage of the timed run (default f32; the others are for profiling)")
     ap.add_argument("--stoch", action="store_true",
                     help="stochastic rounding of the 16-bit storage (profiling)")
+    ap.add_argument("--only", default=None, choices=["batch", "render"],
+                    help="profiling: run one extra alone and print its JSON (batch: "
+                         "--batch-grids grids of the sweep, --euler-steps steps at the "
+                         "fixed shape k=6, rows=16, krows=256, no autotuning; render: "
+                         "the colour map of the --grid state)")
+    ap.add_argument("--batch-grids", type=int, default=512,
+                    help="grids in the sweep of --only batch")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -260,6 +267,8 @@ def main():
         W = H = int(args.grid)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
 
     import torch
     rank, world, local = dist_setup(args.gpus)
@@ -448,13 +457,14 @@ def _render(pkg, stream, h, reps=20):
             "frac": gbs / peak, "peak_kind": kind, "bytes_per_pixel": 16}
 
 
-def _batch_sweep(pkg, stream, steps=5000):
+def _batch_sweep(pkg, stream, steps=5000, n_grids=512, shape=None):
     """Parameter sweep: 512 grids of sizes U{128, 256, 512, 1024}^2, phi ~
     U[0.05, 0.08], eps ~ U[0.02, 0.03], 1-8 disks each (PCG64 seed 4); the
-    autotuner picks the launch shape, then `steps` Euler steps run as one CUDA
-    graph of persistent launches over all grids."""
+    autotuner picks the launch shape (or `shape` = (k, rows, krows) fixes
+    it), then `steps` Euler steps run as one CUDA graph of persistent
+    launches over all grids."""
     import torch
-    spec = ri.sweep_batch(seed=4, n_grids=512)
+    spec = ri.sweep_batch(seed=4, n_grids=n_grids)
     grids = [(n, n) for n in spec.sizes]
     params = [pkg.rdc_params_default(precision=0, eps=e) for e in spec.eps]
     phis = [np.full((n, n), ph, dtype=np.float32) for n, ph in zip(spec.sizes, spec.phi)]
@@ -464,7 +474,11 @@ def _batch_sweep(pkg, stream, steps=5000):
             for (cx, cy, r) in disks:
                 pkg.rdc_batch_seed(b, i, cx, cy, r, ri.SEED_VALUE)
         t0 = time.perf_counter()
-        info = pkg.rdc_batch_tune(b, 3)
+        if shape is None:
+            info = pkg.rdc_batch_tune(b, 3)
+        else:
+            pkg.rdc_batch_set_config(b, *shape, True)
+            info = pkg.rdc_batch_get_info(b)
         tune_s = time.perf_counter() - t0
         pkg.rdc_batch_step(b, None, steps)          # captures the graph (and warms up)
         torch.cuda.synchronize()
@@ -483,6 +497,30 @@ def _batch_sweep(pkg, stream, steps=5000):
                 "tune_seconds": tune_s, "unhealthy_grids": bad}
     finally:
         pkg.rdc_batch_destroy(b)
+
+
+def run_only(args):
+    """One extra alone, for profiling its kernel on a small case."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1901_06535_gb300 as pkg
+    pkg.lib()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    if args.only == "batch":
+        out = _batch_sweep(pkg, stream, steps=args.euler_steps, n_grids=args.batch_grids,
+                           shape=(6, 16, 256))
+    else:
+        h = pkg.rdc_create(W, H, pkg.rdc_params_default(precision=args.precision), None,
+                           stream.cuda_stream)
+        try:
+            for (cx, cy, r) in ri.random_disks(DISK_SEED, N_DISKS, W, H):
+                pkg.rdc_seed(h, cx, cy, r, ri.SEED_VALUE)
+            pkg.rdc_step(h, args.euler_steps)
+            out = _render(pkg, stream, h, reps=args.steps)
+        finally:
+            pkg.rdc_destroy(h)
+    print(json.dumps({"only": args.only, **out}))
 
 
 def _serving(pkg, frames=100, steps_per_frame=50):

@@ -1,8 +1,8 @@
 // Batches of independent grids (parameter sweeps, many sessions): one device
 // allocation per grid (grids can join and leave), a device table of grid
-// descriptors, persistent launches over warp-sized work items of all grids
-// at once, CUDA graphs of whole step sequences, and an autotuner for the
-// launch shape.
+// descriptors, persistent launches whose warps take warp-sized work items of
+// all grids from a queue, CUDA graphs of whole step sequences, and an
+// autotuner for the launch shape.
 //
 // Each grid in a batch runs the same cell_update as a single simulation with
 // the same parameters, so a grid's result is bit-identical whether it is
@@ -53,7 +53,7 @@ struct rdc_batch {
     std::vector<void*> mem;          // per-slot allocation (nullptr = free slot)
     GridDesc* d_desc = nullptr;
     int d_desc_cap = 0;
-    unsigned long long* d_flag = nullptr;
+    unsigned long long* d_flag = nullptr;  // health flag at +0, work queue at +64
     void* stage = nullptr;
     size_t stage_bytes = 0;
     cudaStream_t stream = nullptr;
@@ -88,8 +88,9 @@ void free_graphs(rdc_batch* b)
 
 int persistent_ctas(int nitems)
 {
-    // 128-thread CTAs, 4 warps each; enough CTAs to fill every SM several
-    // times over, never more than the items need
+    // 128-thread CTAs, 4 warps each; enough CTAs to fill every SM with as
+    // many as fit (warps take items from a shared queue, so CTAs beyond that
+    // find it empty and end at once), never more than the items need
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -97,6 +98,9 @@ int persistent_ctas(int nitems)
     const int need = (nitems + 3) / 4;
     return std::max(1, std::min(want, need));
 }
+
+// The two counters of the batched kernels' work queue (zero between launches).
+unsigned* queue_of(rdc_batch* b) { return reinterpret_cast<unsigned*>(b->d_flag) + 16; }
 
 int build_items(rdc_batch* b, bool stream, ItemList* out)
 {
@@ -152,12 +156,12 @@ int enqueue_sequence(rdc_batch* b, int64_t n, int64_t* launches)
         cudaError_t e;
         const long long sbase = (long long)(n - left);  // steps of this call already enqueued
         if (k > 1 && left >= k) {
-            e = launch_batch_stream(b->prec, b->d_desc, sk->dev, sk->n, k, (int)(j & 1), sbase,
-                                    b->sr, persistent_ctas(sk->n), b->stream);
+            e = launch_batch_stream(b->prec, b->d_desc, sk->dev, sk->n, queue_of(b), k,
+                                    (int)(j & 1), sbase, b->sr, persistent_ctas(sk->n), b->stream);
             left -= k;
         } else {
-            e = launch_batch_step1(b->prec, b->d_desc, s1->dev, s1->n, (int)(j & 1), sbase,
-                                   b->sr, persistent_ctas(s1->n), b->stream);
+            e = launch_batch_step1(b->prec, b->d_desc, s1->dev, s1->n, queue_of(b), (int)(j & 1),
+                                   sbase, b->sr, persistent_ctas(s1->n), b->stream);
             left -= 1;
         }
         if (e != cudaSuccess) return host_cuda_fail(e, "batched step kernel");
@@ -328,6 +332,8 @@ int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
         b->owns_stream = true;
     }
     cudaError_t e = cudaMalloc((void**)&b->d_flag, 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flag, 0, 256, b->stream);  // queue zeroed
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         rdc_batch_destroy(b);
         return host_cuda_fail(e, "cudaMalloc(flag)");
@@ -628,10 +634,11 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
         // Every timed launch reads the current buffers (j = 0) and writes the
         // spare ones, so tuning never advances the state.
         auto launch = [&]() {
-            return c.k > 1 ? launch_batch_stream(b->prec, b->d_desc, L->dev, L->n, c.k, 0, 0,
-                                                 b->sr, persistent_ctas(L->n), b->stream)
-                           : launch_batch_step1(b->prec, b->d_desc, L->dev, L->n, 0, 0, b->sr,
-                                                persistent_ctas(L->n), b->stream);
+            return c.k > 1 ? launch_batch_stream(b->prec, b->d_desc, L->dev, L->n, queue_of(b),
+                                                 c.k, 0, 0, b->sr, persistent_ctas(L->n),
+                                                 b->stream)
+                           : launch_batch_step1(b->prec, b->d_desc, L->dev, L->n, queue_of(b),
+                                                0, 0, b->sr, persistent_ctas(L->n), b->stream);
         };
         cudaError_t e = launch();  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);

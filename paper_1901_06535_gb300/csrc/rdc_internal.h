@@ -91,14 +91,17 @@ size_t stepk_smem_bytes(int prec, ShapeK s);
 cudaError_t launch_stream(int prec, const Planes& g, const ModelD& m, int k, int rows,
                           cudaStream_t st);
 // Batched launches over a device item list (persistent: `ctas` CTAs of 128
-// threads, each warp looping over items); launch index j selects buffers.
-// sbase: Euler steps of the call before this launch (the rounding stream's
-// step index is the grid's steps + sbase + level); sr: stochastic rounding.
+// threads; each warp takes the next item from the work queue `queue`, two
+// zeroed counters that the launch leaves zeroed); launch index j selects
+// buffers.  sbase: Euler steps of the call before this launch (the rounding
+// stream's step index is the grid's steps + sbase + level); sr: stochastic
+// rounding.
 cudaError_t launch_batch_step1(int prec, const GridDesc* d, const Item* items, int nitems,
-                               int j, long long sbase, int sr, int ctas, cudaStream_t st);
+                               unsigned* queue, int j, long long sbase, int sr, int ctas,
+                               cudaStream_t st);
 cudaError_t launch_batch_stream(int prec, const GridDesc* d, const Item* items, int nitems,
-                                int k, int j, long long sbase, int sr, int ctas,
-                                cudaStream_t st);
+                                unsigned* queue, int k, int j, long long sbase, int sr,
+                                int ctas, cudaStream_t st);
 // Columns a warp covers (single step) / writes (streamed, k steps).
 int batch_step1_cols(int prec);
 int batch_stream_outc(int prec, int k);

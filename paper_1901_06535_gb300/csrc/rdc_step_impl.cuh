@@ -210,13 +210,12 @@ __device__ __forceinline__ Model<T> model_of(const GridDesc& d)
 template <typename S, int MODE>
 __global__ void __launch_bounds__(128)
 k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
-              int j, long long sbase)
+              unsigned* queue, int j, long long sbase)
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
     pdl_enter();
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
+    for (int it = queue_next(queue); it < nitems; it = queue_next(queue)) {
         const Item item = items[it];
         const GridDesc& d = descs[item.g];
         if (!d.active) continue;
@@ -228,17 +227,19 @@ k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items
                             static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0,
                             item.y0, item.y1, m);
     }
+    queue_done(queue);
 }
 
 template <typename S>
-cudaError_t launch_batch_step1_t(const GridDesc* d, const Item* items, int nitems, int j,
-                                 long long sbase, int sr, int ctas, cudaStream_t st)
+cudaError_t launch_batch_step1_t(const GridDesc* d, const Item* items, int nitems,
+                                 unsigned* queue, int j, long long sbase, int sr, int ctas,
+                                 cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
     if (ctas < 1) return cudaErrorInvalidValue;
     return dispatch_full<S>(sr != 0, [&](auto mc) {
         return launch_pdl(k_step1_batch<S, decltype(mc)::value>, dim3(ctas), dim3(128), 0, st, d,
-                          items, nitems, j, sbase);
+                          items, nitems, queue, j, sbase);
     });
 }
 

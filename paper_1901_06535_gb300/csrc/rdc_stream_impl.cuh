@@ -369,13 +369,12 @@ k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
 template <typename S, int MODE, int K, int N>
 __global__ void __launch_bounds__(128)
 k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
-               int j, long long sbase)
+               unsigned* queue, int j, long long sbase)
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
     pdl_enter();
-    const int nwarps = gridDim.x * (blockDim.x >> 5);
-    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < nitems; it += nwarps) {
+    for (int it = queue_next(queue); it < nitems; it = queue_next(queue)) {
         const Item item = items[it];
         const GridDesc& d = descs[item.g];
         if (!d.active) continue;
@@ -387,6 +386,7 @@ k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ item
             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
             static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0, item.y0, item.y1, m);
     }
+    queue_done(queue);
 }
 
 // Cells per lane.  FP32 and 16-bit storage: 4 for K <= 3 (16-byte FP32
@@ -419,31 +419,33 @@ cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>&
 }
 
 template <typename S, int K>
-cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nitems, int j,
-                                  long long sbase, bool sr, int ctas, cudaStream_t st)
+cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nitems,
+                                  unsigned* queue, int j, long long sbase, bool sr, int ctas,
+                                  cudaStream_t st)
 {
     constexpr int N = StreamVec<S, K>::N;
     return dispatch_full<S>(sr, [&](auto mc) {
         return launch_pdl(k_stream_batch<S, decltype(mc)::value, K, N>, dim3(ctas), dim3(128), 0,
-                          st, d, items, nitems, j, sbase);
+                          st, d, items, nitems, queue, j, sbase);
     });
 }
 
 template <typename S>
-cudaError_t launch_batch_stream_t(const GridDesc* d, const Item* items, int nitems, int k,
-                                  int j, long long sbase, int sr, int ctas, cudaStream_t st)
+cudaError_t launch_batch_stream_t(const GridDesc* d, const Item* items, int nitems,
+                                  unsigned* queue, int k, int j, long long sbase, int sr,
+                                  int ctas, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
     if (ctas < 1) return cudaErrorInvalidValue;
     const bool r = sr != 0;
     switch (k) {
-        case 2: return launch_stream_batch_k<S, 2>(d, items, nitems, j, sbase, r, ctas, st);
-        case 3: return launch_stream_batch_k<S, 3>(d, items, nitems, j, sbase, r, ctas, st);
-        case 4: return launch_stream_batch_k<S, 4>(d, items, nitems, j, sbase, r, ctas, st);
-        case 5: return launch_stream_batch_k<S, 5>(d, items, nitems, j, sbase, r, ctas, st);
-        case 6: return launch_stream_batch_k<S, 6>(d, items, nitems, j, sbase, r, ctas, st);
-        case 7: return launch_stream_batch_k<S, 7>(d, items, nitems, j, sbase, r, ctas, st);
-        case 8: return launch_stream_batch_k<S, 8>(d, items, nitems, j, sbase, r, ctas, st);
+        case 2: return launch_stream_batch_k<S, 2>(d, items, nitems, queue, j, sbase, r, ctas, st);
+        case 3: return launch_stream_batch_k<S, 3>(d, items, nitems, queue, j, sbase, r, ctas, st);
+        case 4: return launch_stream_batch_k<S, 4>(d, items, nitems, queue, j, sbase, r, ctas, st);
+        case 5: return launch_stream_batch_k<S, 5>(d, items, nitems, queue, j, sbase, r, ctas, st);
+        case 6: return launch_stream_batch_k<S, 6>(d, items, nitems, queue, j, sbase, r, ctas, st);
+        case 7: return launch_stream_batch_k<S, 7>(d, items, nitems, queue, j, sbase, r, ctas, st);
+        case 8: return launch_stream_batch_k<S, 8>(d, items, nitems, queue, j, sbase, r, ctas, st);
     }
     return cudaErrorInvalidValue;
 }
