@@ -367,9 +367,9 @@ k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
 
 // Persistent k-step launch over a batch of grids (see k_step1_batch).
 template <typename S, int MODE, int K, int N>
-__global__ void __launch_bounds__(128)
-k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
-               unsigned* queue, int j, long long sbase)
+__device__ __forceinline__ void stream_batch_body(const GridDesc* __restrict__ descs,
+                                                  const Item* __restrict__ items, int nitems,
+                                                  unsigned* queue, int j, long long sbase)
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
@@ -387,6 +387,35 @@ k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ item
             static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0, item.y0, item.y1, m);
     }
     queue_done(queue);
+}
+
+template <typename S, int MODE, int K, int N>
+__global__ void __launch_bounds__(128)
+k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
+               unsigned* queue, int j, long long sbase)
+{
+    stream_batch_body<S, MODE, K, N>(descs, items, nitems, queue, j, sbase);
+}
+
+// The same kernel with its registers capped so that MINB CTAs fit on an SM.
+template <typename S, int MODE, int K, int N, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+k_stream_batch_capped(const GridDesc* __restrict__ descs, const Item* __restrict__ items,
+                      int nitems, unsigned* queue, int j, long long sbase)
+{
+    stream_batch_body<S, MODE, K, N>(descs, items, nitems, queue, j, sbase);
+}
+
+// CTAs per SM that the batched kernel is compiled for, 0 = the compiler's
+// choice.  FP32 at K = 5 and 6 is capped at 6 and 5 CTAs (80 and 96
+// registers instead of 92 and 111, no spills): measured on the 512-grid sweep,
+// K = 5 793 -> 807 and K = 6 784 -> 827 G cell-updates/s, identical bits.  At
+// K = 7 and 8 the same caps spill; an explicit cap of 1 elsewhere would change
+// the compiler's allocation (K = 4: 72 -> 110 registers).
+template <typename S, int K>
+constexpr int batch_stream_min_ctas()
+{
+    return sizeof(S) != 4 ? 0 : (K == 5 ? 6 : (K == 6 ? 5 : 0));
 }
 
 // Cells per lane.  FP32 and 16-bit storage: 4 for K <= 3 (16-byte FP32
@@ -425,8 +454,13 @@ cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nite
 {
     constexpr int N = StreamVec<S, K>::N;
     return dispatch_full<S>(sr, [&](auto mc) {
-        return launch_pdl(k_stream_batch<S, decltype(mc)::value, K, N>, dim3(ctas), dim3(128), 0,
-                          st, d, items, nitems, queue, j, sbase);
+        constexpr int MINB = batch_stream_min_ctas<S, K>();
+        if constexpr (MINB > 0)
+            return launch_pdl(k_stream_batch_capped<S, decltype(mc)::value, K, N, MINB>,
+                              dim3(ctas), dim3(128), 0, st, d, items, nitems, queue, j, sbase);
+        else
+            return launch_pdl(k_stream_batch<S, decltype(mc)::value, K, N>, dim3(ctas),
+                              dim3(128), 0, st, d, items, nitems, queue, j, sbase);
     });
 }
 

@@ -63,7 +63,7 @@ def _read(pkg, b, i, W, H):
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
-@pytest.mark.parametrize("k", [1, 3, 4])
+@pytest.mark.parametrize("k", [1, 3, 4, 5, 6, 8])
 def test_batch_equals_solo(gpu, prec, k):
     n = 2 * k + 5 if k > 1 else 13
     b, setups = _make_batch(gpu, prec, k)
@@ -125,6 +125,41 @@ def test_batch_subsets_and_graphs(gpu):
             assert np.array_equal(u, us) and np.array_equal(v, vs), (i, counts[i])
     finally:
         gpu.rdc_batch_destroy(b)
+
+
+def test_two_batches_on_two_streams(gpu):
+    """Two batches stepped concurrently on their own streams (each batch's
+    work queue is its own): every grid equals the same grid run alone."""
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    made = []
+    try:
+        for st, k in ((s1, 6), (s2, 5)):
+            grids, params, phis, setups = [], [], [], []
+            for i, (W, H) in enumerate(SIZES):
+                eps, phi, disks = _grid_setup(i, W, H)
+                grids.append((W, H))
+                params.append(gpu.rdc_params_default(precision=0, eps=eps, k_block=k))
+                phis.append(np.full((H, W), phi, dtype=np.float32))
+                setups.append((eps, phi, disks))
+            b = gpu.rdc_batch_create(grids, params, phis, stream=st.cuda_stream)
+            made.append((b, setups))
+            for i, (_, _, disks) in enumerate(setups):
+                for d in disks:
+                    gpu.rdc_batch_seed(b, i, *d)
+        for _ in range(6):                  # interleaved, no host sync between
+            for b, _ in made:
+                gpu.rdc_batch_step(b, None, 11)
+        torch.cuda.synchronize()
+        for b, setups in made:
+            for i, (W, H) in enumerate(SIZES):
+                eps, phi, disks = setups[i]
+                u, v = _read(gpu, b, i, W, H)
+                us, vs = _solo(gpu, W, H, eps, float(np.float32(phi)), disks, 66, "f32")
+                assert np.array_equal(u, us) and np.array_equal(v, vs), (i, W, H)
+    finally:
+        for b, _ in made:
+            gpu.rdc_batch_destroy(b)
 
 
 def test_batch_tune_keeps_state(gpu):
