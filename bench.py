@@ -527,7 +527,8 @@ def _serving(pkg, frames=100, steps_per_frame=50):
     """Interactive serving: 64 sessions arriving Poisson at 20/s (seed 5),
     grids U{512, 1024, 2048}^2 with diode maps at random positions and
     orientations, each requesting `frames` frames of `steps_per_frame` steps
-    with a u = 0.8 touch before each; continuous batching on one stream."""
+    with a u = 0.8 touch before each; continuous batching, one batch and
+    stream per size class."""
     from paper_1901_06535_gb300 import serve
     specs = ri.diode_sessions(seed=5, n=64, frames=frames)
     sessions = [serve.Session(s.sid, s.size, s.size, phi=s.phi, frames=frames,

@@ -5,13 +5,15 @@ have on a tablet, §3) share one GPU.  Each session asks for frames: apply a
 touch (catalytic stimulation, §2), then advance ``steps_per_frame`` Euler
 steps (the paper's "render rate", §2).  The server
 
-  * keeps every admitted session's state on the device (a rdc_batch slot);
+  * keeps every admitted session's state on the device (a slot of one of a
+    few batches, one per size class, each with its own CUDA stream, so that
+    small sessions' frames do not queue behind large ones);
   * admits waiting sessions whenever the device-memory budget and the session
     slots allow, and frees a session's memory when it leaves;
   * every tick gathers all sessions that have a pending frame and no frame in
-    flight, applies their touches and advances all of them with one batched
-    launch sequence (a session arriving while others are on the GPU joins the
-    next tick, so its work overlaps theirs on the device);
+    flight, applies their touches and advances them with one batched launch
+    sequence per size class (a session arriving while others are on the GPU
+    joins the next tick, so its work overlaps theirs on the device);
   * detects completion with CUDA events and records each frame's latency from
     request to completion.
 
@@ -40,6 +42,7 @@ class Session:
     frames: int = 10                        # frames the session will request
     touches: list = dataclasses.field(default_factory=list)  # per frame (cx, cy, r, value) or None
     # filled in by the server
+    lane: int = -1
     slot: int = -1
     done_frames: int = 0
     arrival: float = 0.0
@@ -64,25 +67,37 @@ class Frame:
         return self.completed - self.requested
 
 
+class _Lane:
+    """One size class: a batch of its sessions and the stream it runs on."""
+
+    def __init__(self, params, k_block: int, graphs: bool, stream):
+        self.stream = stream
+        self.batch = C.rdc_batch_create([], [params], stream=stream.cuda_stream)
+        C.rdc_batch_set_config(self.batch, max(1, k_block), 8, 64, graphs)
+
+
 class Server:
     def __init__(self, precision=C.RDC_F32, k_block: int = 6, steps_per_frame: int = 50,
                  memory_budget: int | None = None, max_sessions: int = 1 << 30,
-                 stream=None, graphs: bool = False, flags: int = 0):
+                 stream=None, graphs: bool = False, flags: int = 0,
+                 lane_cells: tuple = (1 << 19, 1 << 21)):
         """k_block: Euler steps per batched launch (6 measured best for the
         p99 frame latency of the 64-session diode workload: 3.4 ms vs 3.7 ms
         at 4); flags: 0 or RDC_STOCH_ROUND (16-bit storage), for every
-        session."""
+        session.  lane_cells: upper cell counts of the size classes (a last
+        class takes the rest); each class has its own batch and stream, or
+        all share `stream` when one is given."""
         import torch
         self.torch = torch
         self.precision = precision
         self.flags = int(flags)
         self.steps = int(steps_per_frame)
         self.params = C.rdc_params_default(precision=precision, k_block=k_block, flags=self.flags)
-        if stream is None:
-            stream = torch.cuda.Stream()
-        self.stream = stream
-        self.batch = C.rdc_batch_create([], [self.params], stream=stream.cuda_stream)
-        C.rdc_batch_set_config(self.batch, max(1, k_block), 8, 64, graphs)
+        self.lane_cells = tuple(int(c) for c in lane_cells)
+        self.lanes = []
+        for _ in range(len(self.lane_cells) + 1):
+            st = stream if stream is not None else torch.cuda.Stream()
+            self.lanes.append(_Lane(self.params, k_block, graphs, st))
         if memory_budget is None:
             free, _ = torch.cuda.mem_get_info()
             memory_budget = int(free * 0.8)
@@ -116,7 +131,8 @@ class Server:
                                      round_seed=s.round_seed if self.flags else 0)
             if s.eps is not None:
                 p.eps = s.eps
-            s.slot = C.rdc_batch_add(self.batch, s.width, s.height, p, s.phi)
+            s.lane = self._lane_of(s)
+            s.slot = C.rdc_batch_add(self.lanes[s.lane].batch, s.width, s.height, p, s.phi)
             s.admitted_at = time.perf_counter()
             self.used += need
             self.waiting.popleft()
@@ -124,12 +140,19 @@ class Server:
             self.peak_sessions = max(self.peak_sessions, len(self.active))
             self._request(s)
 
+    def _lane_of(self, s: Session) -> int:
+        cells = s.width * s.height
+        for i, c in enumerate(self.lane_cells):
+            if cells <= c:
+                return i
+        return len(self.lane_cells)
+
     def _request(self, s: Session):
         if s.done_frames < s.frames:
             self.pending[s.sid] = Frame(s.sid, s.done_frames, time.perf_counter())
 
     def _leave(self, s: Session):
-        C.rdc_batch_remove(self.batch, s.slot)
+        C.rdc_batch_remove(self.lanes[s.lane].batch, s.slot)
         self.used -= s.state_bytes(self.precision)
         del self.active[s.sid]
         self._admit()
@@ -137,26 +160,32 @@ class Server:
     # -- the loop -------------------------------------------------------------
     def tick(self) -> int:
         """Launches one batched frame for every session with a pending
-        request and none in flight.  Returns the number of sessions stepped."""
+        request and none in flight, one launch sequence per size class.
+        Returns the number of sessions stepped."""
         busy = {f.sid for _, fs in self.inflight for f in fs}
         ready = [sid for sid in self.pending if sid not in busy]
         if not ready:
             return 0
-        frames = []
-        slots = []
+        by_lane: dict[int, list[int]] = {}
         for sid in ready:
-            s = self.active[sid]
-            f = self.pending.pop(sid)
-            t = s.touches[f.index] if f.index < len(s.touches) else None
-            if t is not None:
-                C.rdc_batch_seed(self.batch, s.slot, *t)
-            slots.append(s.slot)
-            frames.append(f)
-            self.cells_stepped += s.width * s.height * self.steps
-        C.rdc_batch_step(self.batch, slots, self.steps)
-        ev = self.torch.cuda.Event()
-        ev.record(self.stream)
-        self.inflight.append((ev, frames))
+            by_lane.setdefault(self.active[sid].lane, []).append(sid)
+        for li, sids in sorted(by_lane.items()):
+            lane = self.lanes[li]
+            frames = []
+            slots = []
+            for sid in sids:
+                s = self.active[sid]
+                f = self.pending.pop(sid)
+                t = s.touches[f.index] if f.index < len(s.touches) else None
+                if t is not None:
+                    C.rdc_batch_seed(lane.batch, s.slot, *t)
+                slots.append(s.slot)
+                frames.append(f)
+                self.cells_stepped += s.width * s.height * self.steps
+            C.rdc_batch_step(lane.batch, slots, self.steps)
+            ev = self.torch.cuda.Event()
+            ev.record(lane.stream)
+            self.inflight.append((ev, frames))
         self.ticks += 1
         return len(ready)
 
@@ -209,13 +238,14 @@ class Server:
     def read(self, s: Session, dtype=np.float64):
         u = np.empty((s.height, s.width), dtype=dtype)
         v = np.empty_like(u)
-        C.rdc_batch_read(self.batch, s.slot, u, v)
+        C.rdc_batch_read(self.lanes[s.lane].batch, s.slot, u, v)
         return u, v
 
     def close(self):
-        if self.batch:
-            C.rdc_batch_destroy(self.batch)
-            self.batch = None
+        for lane in self.lanes:
+            if lane.batch:
+                C.rdc_batch_destroy(lane.batch)
+                lane.batch = None
 
     def stats(self) -> dict:
         lat = np.array([f.latency for f in self.completed]) * 1e3

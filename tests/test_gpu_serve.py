@@ -164,3 +164,30 @@ def test_serving_stochastic_rounding_mix_equals_alone(gpu):
         u, v = finals[s.sid]
         ua, va = _alone(gpu, s, 14, precision=2, flags=4)
         assert np.array_equal(u, ua) and np.array_equal(v, va), s.sid
+
+
+def test_serving_size_classes_equal_alone(gpu):
+    """Sessions split over three size classes (each its own batch and
+    stream, stepping concurrently): every session equals its solo run."""
+    from paper_1901_06535_gb300 import serve
+    sessions = _sessions(serve, 9, seed=41, frames=5)
+    srv = serve.Server(precision=0, k_block=6, steps_per_frame=18, lane_cells=(4000, 10000))
+    finals = {}
+    lanes = {}
+    orig_leave = srv._leave
+
+    def leave(s):
+        finals[s.sid] = srv.read(s)
+        lanes[s.sid] = s.lane
+        orig_leave(s)
+
+    srv._leave = leave
+    try:
+        serve.run_workload(sessions, [0.0005 * i for i in range(len(sessions))], srv)
+    finally:
+        srv.close()
+    assert len(set(lanes.values())) >= 2, lanes
+    for s in sessions:
+        u, v = finals[s.sid]
+        ua, va = _alone(gpu, s, 18)
+        assert np.array_equal(u, ua) and np.array_equal(v, va), s.sid
