@@ -82,8 +82,8 @@ class Server:
                  stream=None, graphs: bool = False, flags: int = 0,
                  lane_cells: tuple = (1 << 19, 1 << 21)):
         """k_block: Euler steps per batched launch (6 measured best for the
-        p99 frame latency of the 64-session diode workload: 3.4 ms vs 3.7 ms
-        at 4); flags: 0 or RDC_STOCH_ROUND (16-bit storage), for every
+        p99 frame latency of the 64-session diode workload with three size
+        classes: 1.6-1.7 ms; 8: 1.6-1.8; 4 and 5: 3.1-3.4); flags: 0 or RDC_STOCH_ROUND (16-bit storage), for every
         session.  lane_cells: upper cell counts of the size classes (a last
         class takes the rest); each class has its own batch and stream, or
         all share `stream` when one is given."""
