@@ -42,14 +42,14 @@ def _max_at_output(pkg, c, fire, prec, flags=0, round_seed=0):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_c2_truth_table(gpu, prec):
+def test_andgate_1024_truth_table(gpu, prec):
     c = _circuit()
     out = {tuple(f): _max_at_output(gpu, c, f, prec) > 0.3
            for f in ([], ["A"], ["B"], ["A", "B"])}
     assert out == {(): False, ("A",): False, ("B",): False, ("A", "B"): True}, out
 
 
-def test_c2_output_arrival_f32_vs_f64(gpu, record_property):
+def test_andgate_1024_output_arrival_f32_vs_f64(gpu, record_property):
     c = _circuit()
     seeds = [(*c.seeds["A"], 0.8), (*c.seeds["B"], 0.8)]
     t = {}
@@ -62,7 +62,7 @@ def test_c2_output_arrival_f32_vs_f64(gpu, record_property):
     assert t["f64"] > 0 and abs(t["f32"] - t["f64"]) <= 0.01 * t["f64"], t
 
 
-def test_c2_bf16_reported(gpu, record_property):
+def test_andgate_1024_bf16_reported(gpu, record_property):
     """BF16 storage on the same circuit: reported, not gated (the gate's
     window is about 2 % of the band's phi; BF16 shifts fronts by ~1 %)."""
     c = _circuit()
@@ -73,7 +73,7 @@ def test_c2_bf16_reported(gpu, record_property):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "f16"])
-def test_c2_stochastic_rounding_truth_table(gpu, prec, record_property):
+def test_andgate_1024_stochastic_rounding_truth_table(gpu, prec, record_property):
     """16-bit storage with stochastic rounding (RDC_STOCH_ROUND) on the same
     circuit, three keys: the AND truth table holds for each.  (BF16 with
     round-to-nearest loses it: v stagnates and the colliding fronts do not
@@ -90,10 +90,10 @@ def test_c2_stochastic_rounding_truth_table(gpu, prec, record_property):
         assert t == {"-": False, "A": False, "B": False, "AB": True}, (seed, t)
 
 
-def test_c2_maxabs_1000_reported(gpu, record_property):
-    """Pointwise max-abs of u against FP64 after 1000 steps of the C2 workload
-    (both inputs fired), for each reduced mode: reported, with a sanity
-    bound.  FP64 on the GPU is the oracle's result bit for bit (tested
+def test_andgate_1024_maxabs_1000_reported(gpu, record_property):
+    """Pointwise max-abs of u against FP64 after 1000 steps of the 1024²
+    AND-gate workload (both inputs fired), for each reduced mode: reported,
+    with a sanity bound.  FP64 on the GPU is the oracle's result bit for bit (tested
     elsewhere), so it stands in for the oracle at this size."""
     c = _circuit()
     seeds = [(*c.seeds["A"], 0.8), (*c.seeds["B"], 0.8)]
@@ -104,6 +104,6 @@ def test_c2_maxabs_1000_reported(gpu, record_property):
         u, _, _ = gpu_run(gpu, N, N, phi=c.phi.astype(np.float32), seeds=seeds, n=1000,
                           prec=prec, k=4, flags=flags, round_seed=1 if flags else 0)
         out[name] = float(np.max(np.abs(u - ref)))
-    record_property("c2_maxabs_u_1000", out)
-    print("C2 max-abs of u vs FP64 after 1000 steps:", {k: f"{v:.2e}" for k, v in out.items()})
+    record_property("andgate_1024_maxabs_u_1000", out)
+    print("1024² AND gate: max-abs of u vs FP64 after 1000 steps:", {k: f"{v:.2e}" for k, v in out.items()})
     assert out["f32"] < 0.05 and all(v < 0.9 for v in out.values())

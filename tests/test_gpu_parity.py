@@ -76,7 +76,7 @@ def test_f64_bitwise(gpu, orc, om, W, H, flags):
 
 
 @pytest.mark.parametrize("k", [1, 4])
-def test_f64_c1_workload_bitwise(gpu, orc, om, k):
+def test_f64_256_single_disk_bitwise(gpu, orc, om, k):
     """256 x 256, uniform phi = 0.054, rest state, disk r = 6 at the centre set
     to u = 0.8, 1000 steps: FP64 GPU equals the oracle bit for bit (so the
     1e-12 max-abs target holds with margin zero)."""
@@ -209,9 +209,10 @@ ARRIVAL_TOL = 0.01
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
-def test_arrival_times_c1(gpu, orc, om, prec, record_property):
-    """C1 geometry extended in time: the front's arrival at probes 20, 40 and
-    60 cells from the seed agrees with the FP64 oracle within 1 %."""
+def test_arrival_times_256_single_disk(gpu, orc, om, prec, record_property):
+    """The 256² single-disk geometry extended in time: the front's arrival at
+    probes 20, 40 and 60 cells from the seed agrees with the FP64 oracle
+    within 1 %."""
     W = H = 256
     seeds = [(127.5, 127.5, 6.0, 0.8)]
     probes = ri.axis_probes(W, H, (20, 40, 60))
@@ -235,15 +236,15 @@ MAXABS_BOUND = {"f32": 0.05, "f16": 0.05, "bf16": 0.9}
 
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
 def test_maxabs_1000_steps_reported(gpu, orc, om, prec, record_property):
-    """Max-abs difference from FP64 after 1000 C1 steps: reported, with a
-    per-precision sanity bound (no divergence)."""
+    """Max-abs difference from FP64 after 1000 steps of the 256² single-disk
+    workload: reported, with a per-precision sanity bound (no divergence)."""
     W = H = 256
     seeds = [(127.5, 127.5, 6.0, 0.8)]
     u, _, _ = gpu_run(gpu, W, H, seeds=seeds, n=1000, prec=prec, k=4)
     ref = orc_run(orc, om, W, H, seeds=seeds, n=1000)
     err = float(np.max(np.abs(u - ref["u"])))
     record_property("maxabs_u_1000", err)
-    print(f"maxabs u vs FP64 oracle after 1000 C1 steps [{prec}]: {err:.3e}")
+    print(f"maxabs u vs FP64 oracle after 1000 steps, 256² single disk [{prec}]: {err:.3e}")
     assert err < MAXABS_BOUND[prec]
 
 

@@ -9,7 +9,7 @@
   diffusion-only model, whose per-step change is far below half a storage
   spacing, stays frozen under round-to-nearest but decays at the closed-form
   rate (1 + dt Du lambda)^n under stochastic rounding.
-* The C1 front's arrival times stay within 1 % of the FP64 oracle."""
+* The 256² single-disk workload's front arrival times stay within 1 % of the FP64 oracle."""
 from __future__ import annotations
 
 import numpy as np
@@ -140,7 +140,7 @@ def test_stochastic_rounding_follows_the_diffusion_decay(gpu, prec):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "f16"])
-def test_arrival_times_c1_stochastic(gpu, orc, om, prec, record_property):
+def test_arrival_times_256_single_disk_stochastic(gpu, orc, om, prec, record_property):
     W = H = 256
     seeds = [(127.5, 127.5, 6.0, 0.8)]
     probes = ri.axis_probes(W, H, (20, 40, 60))
