@@ -442,9 +442,9 @@ int rdc_set_shape(rdc_sim* sim, const rdc_launch_shape* in);
  * Scratch: intermediate states of multi-step calls and the health flag live
  * in one file-scope device array of 32 MiB that every GPU loading this
  * library holds until the process exits.  A grid needs 256 + 2 *
- * roundup256(pitch_bytes * H) bytes of it (FP32: about 4 M cells, e.g.
- * 2048 x 2048); larger grids get RDC_EUNSUPPORTED before anything is
- * enqueued.  The first call on each device looks the array's address up
+ * roundup256(pitch_bytes * H) bytes of it (FP32: just under 4 M cells, e.g.
+ * 2048 x 2047; 2048 x 2048 is 256 bytes over); larger grids get
+ * RDC_EUNSUPPORTED before anything is enqueued.  The first call on each device looks the array's address up
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  Every call shares the array and it keeps the
  * previous call's contents (the flag is reset on every call): calls whose

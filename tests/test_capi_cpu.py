@@ -189,3 +189,21 @@ def test_noalloc_refuses_stochastic_rounding(librdc):
                             fake + 8192, fake + 12288, fake + 16384, 64, 3, None,
                             ctypes.byref(bad))
     assert rc == librdc.RDC_EINVAL
+
+
+def test_noalloc_scratch_limit_is_exact(librdc):
+    """The static scratch (32 MiB) holds a 256-byte flag area and two state
+    planes of roundup256(pitch * H) bytes: 2048 x 2048 FP32 (two 16 MiB
+    planes) is 256 bytes over and is refused with RDC_EUNSUPPORTED before any
+    device call (fake, never dereferenced addresses); so are the 16-bit and
+    FP64 grids of the same plane size."""
+    import ctypes
+    L = librdc.lib()
+    from paper_1901_06535_gb300._capi import rdc_grid
+    fake = 1 << 40
+    for prec, (w, h), esz in ((0, (2048, 2048), 4), (2, (4096, 2048), 2), (1, (1024, 2048), 8)):
+        p = librdc.rdc_params_default(precision=prec)
+        rc = L.rdc_step_noalloc(rdc_grid(w, h), ctypes.byref(p), fake, fake + 4096,
+                                fake + 8192, fake + 12288, fake + 16384, w * esz, 3, None,
+                                None)
+        assert rc == librdc.RDC_EUNSUPPORTED, (prec, rc)
