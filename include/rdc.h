@@ -401,17 +401,22 @@ typedef struct {
  * Autotuner: times reps launches of each candidate shape (single step with
  * 4..32 rows per CTA; k in {2, 3, 4, 6, 8} with the register-streamed kernel
  * at 32..256 rows per CTA -- full model only -- and with the shared-memory
- * tile kernel), keeps the fastest in cell-updates per second and reports it
- * in *out and *best_gcups (both optional).  Every timed launch reads the
- * current state and writes the spare buffers, so tuning neither advances nor
- * changes the state, and any pick gives the same bits.
+ * tile kernel; on grids so tall that a shape would need more than 65535 CTA
+ * rows, that shape is skipped), keeps the fastest in cell-updates per second
+ * and reports it in *out and *best_gcups (both optional).  Every timed launch
+ * reads the current state and writes the spare buffers, so tuning neither
+ * advances nor changes the state, and any pick gives the same bits.
  */
 int rdc_tune(rdc_sim* sim, int32_t reps, rdc_launch_shape* out, double* best_gcups);
 
 /* Current launch shapes (set at create from the grid size and k_block). */
 int rdc_get_shape(rdc_sim* sim, rdc_launch_shape* out);
 
-/* Replaces the launch shapes; RDC_EINVAL (and no change) if out of range. */
+/* Replaces the launch shapes; RDC_EINVAL (and no change) if out of range:
+ * bx not in 32..256 or not a multiple of 32, rows < 1, k outside 1..8,
+ * nthreads not in 32..512 or not a multiple of 32, variant outside 0..1,
+ * krows < 1, a tile needing more than 227 KB of shared memory, or (k > 1)
+ * more than 65535 CTA rows at krows or ty rows each. */
 int rdc_set_shape(rdc_sim* sim, const rdc_launch_shape* in);
 
 /*
