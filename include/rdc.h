@@ -551,6 +551,11 @@ int rdc_batch_set_config(rdc_batch* b, int32_t k, int32_t rows, int32_t krows, i
  * RDC_EINVAL if b or out is NULL. */
 int rdc_batch_get_info(rdc_batch* b, rdc_batch_info* out);
 
+/* Host only.  Width and height of grid idx (the sizes of the host arrays that
+ * rdc_batch_set_state and rdc_batch_read take).  RDC_EINVAL if b or out is
+ * NULL or idx is not a live grid. */
+int rdc_batch_get_grid(rdc_batch* b, int32_t idx, rdc_grid* out);
+
 /*
  * Autotuner: times reps launches of each candidate (single step with 8, 16 or
  * 32 rows per item; k in {2, 3, 4, 6, 8} with 32..256 rows per item) over all

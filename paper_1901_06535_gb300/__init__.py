@@ -20,8 +20,8 @@ from ._capi import (  # noqa: F401  (re-exported C-ABI names)
     rdc_probe, rdc_read, rdc_reset_rest, rdc_rest_state, rdc_seed, rdc_set_phi,
     rdc_set_shape, rdc_set_state, rdc_stability, rdc_status_str, rdc_step, rdc_step_noalloc,
     rdc_sync, rdc_batch_add, rdc_batch_check, rdc_batch_create, rdc_batch_destroy,
-    rdc_batch_get_info, rdc_batch_read, rdc_batch_remove, rdc_batch_seed, rdc_batch_set_config,
-    rdc_batch_set_state, rdc_batch_step, rdc_batch_sync, rdc_batch_tune,
+    rdc_batch_get_grid, rdc_batch_get_info, rdc_batch_read, rdc_batch_remove, rdc_batch_seed,
+    rdc_batch_set_config, rdc_batch_set_state, rdc_batch_step, rdc_batch_sync, rdc_batch_tune,
     RDC_RENDER_SNAPSHOT, RDC_RENDER_TIMELAPSE, rdc_render, rdc_timelapse_record, rdc_tune,
     RDC_SNAP_DEGREES, RDC_WIDTH_IMPERMEABLE, RDC_WIDTH_PERMEABLE, RDC_WIDTH_SEMIPERMEABLE,
     rdc_draw_line, rdc_fill_phi, rdc_read_phi, rdc_snap_segment, rdc_check_division,

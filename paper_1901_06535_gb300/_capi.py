@@ -156,6 +156,7 @@ _SIGS = {
     "rdc_batch_set_config": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int32]),
     "rdc_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(rdc_batch_info)]),
+    "rdc_batch_get_grid": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_grid)]),
     "rdc_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_batch_info)]),
     "rdc_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_launch_shape),
                                 ctypes.POINTER(ctypes.c_double)]),
@@ -231,6 +232,20 @@ def _host_ptr(a, what: str):
     if a.dtype not in codes:
         raise ValueError(f"{what}: unsupported dtype {a.dtype}")
     return a.ctypes.data, codes[a.dtype], a.shape
+
+
+def _check_cells(shape, width: int, height: int, what: str):
+    """A host array handed to the library must hold exactly one value per
+    cell (the library reads or writes width * height of them)."""
+    if shape is not None and int(np.prod(shape)) != width * height:
+        raise ValueError(f"{what}: {tuple(shape)} holds {int(np.prod(shape))} values, "
+                         f"the grid has {height} x {width} cells")
+
+
+def _same_code(cu, cv, what: str):
+    if cu is not None and cv is not None and cu != cv:
+        raise ValueError(f"{what} must have the same dtype")
+    return cu if cu is not None else cv
 
 
 CUDA_STREAM_LEGACY = 0x1
@@ -324,7 +339,9 @@ def rdc_destroy(h) -> None:
 
 
 def rdc_set_phi(h, phi) -> int:
-    ptr, code, _ = _host_ptr(phi, "phi")
+    ptr, code, shape = _host_ptr(phi, "phi")
+    view = rdc_get_view(h)
+    _check_cells(shape, view.width, view.height, "phi")
     return _chk(lib().rdc_set_phi(h, ptr, code), "rdc_set_phi")
 
 
@@ -345,13 +362,14 @@ def rdc_seed(h, cx: float, cy: float, r: float, value: float) -> int:
 
 
 def rdc_set_state(h, u=None, v=None) -> int:
-    pu, cu, _ = _host_ptr(u, "u")
-    pv, cv, _ = _host_ptr(v, "v")
-    if cu is not None and cv is not None and cu != cv:
-        raise ValueError("u and v must have the same dtype")
-    code = cu if cu is not None else cv
+    pu, cu, su = _host_ptr(u, "u")
+    pv, cv, sv = _host_ptr(v, "v")
+    code = _same_code(cu, cv, "u and v")
     if code is None:
         return RDC_OK
+    view = rdc_get_view(h)
+    _check_cells(su, view.width, view.height, "u")
+    _check_cells(sv, view.width, view.height, "v")
     return _chk(lib().rdc_set_state(h, pu, pv, code), "rdc_set_state")
 
 
@@ -362,11 +380,15 @@ def rdc_step(h, n: int) -> int:
 def rdc_read(h, u_out=None, v_out=None):
     """Fills caller-owned host arrays (same dtype); returns the status
     (RDC_OK or RDC_ENONFINITE)."""
-    pu, cu, _ = _host_ptr(u_out, "u_out")
-    pv, cv, _ = _host_ptr(v_out, "v_out")
-    if cu is not None and cv is not None and cu != cv:
-        raise ValueError("u_out and v_out must have the same dtype")
-    code = cu if cu is not None else (cv if cv is not None else RDC_DTYPE_F64)
+    pu, cu, su = _host_ptr(u_out, "u_out")
+    pv, cv, sv = _host_ptr(v_out, "v_out")
+    code = _same_code(cu, cv, "u_out and v_out")
+    if code is None:
+        code = RDC_DTYPE_F64
+    else:
+        view = rdc_get_view(h)
+        _check_cells(su, view.width, view.height, "u_out")
+        _check_cells(sv, view.width, view.height, "v_out")
     return _chk(lib().rdc_read(h, pu, pv, code), "rdc_read", allow=(RDC_ENONFINITE,))
 
 
@@ -581,12 +603,22 @@ def rdc_batch_seed(b, idx: int, cx: float, cy: float, r: float, value: float) ->
                 "rdc_batch_seed")
 
 
+def rdc_batch_get_grid(b, idx: int):
+    """(width, height) of grid idx."""
+    g = rdc_grid()
+    _chk(lib().rdc_batch_get_grid(b, int(idx), ctypes.byref(g)), "rdc_batch_get_grid")
+    return g.width, g.height
+
+
 def rdc_batch_set_state(b, idx: int, u=None, v=None) -> int:
-    pu, cu, _ = _host_ptr(u, "u")
-    pv, cv, _ = _host_ptr(v, "v")
-    code = cu if cu is not None else cv
+    pu, cu, su = _host_ptr(u, "u")
+    pv, cv, sv = _host_ptr(v, "v")
+    code = _same_code(cu, cv, "u and v")
     if code is None:
         return RDC_OK
+    w, h = rdc_batch_get_grid(b, idx)
+    _check_cells(su, w, h, "u")
+    _check_cells(sv, w, h, "v")
     return _chk(lib().rdc_batch_set_state(b, int(idx), pu, pv, code), "rdc_batch_set_state")
 
 
@@ -605,9 +637,15 @@ def rdc_batch_check(b, idx: int):
 
 
 def rdc_batch_read(b, idx: int, u_out=None, v_out=None) -> int:
-    pu, cu, _ = _host_ptr(u_out, "u_out")
-    pv, cv, _ = _host_ptr(v_out, "v_out")
-    code = cu if cu is not None else (cv if cv is not None else RDC_DTYPE_F64)
+    pu, cu, su = _host_ptr(u_out, "u_out")
+    pv, cv, sv = _host_ptr(v_out, "v_out")
+    code = _same_code(cu, cv, "u_out and v_out")
+    if code is None:
+        code = RDC_DTYPE_F64
+    else:
+        w, h = rdc_batch_get_grid(b, idx)
+        _check_cells(su, w, h, "u_out")
+        _check_cells(sv, w, h, "v_out")
     return _chk(lib().rdc_batch_read(b, int(idx), pu, pv, code), "rdc_batch_read",
                 allow=(RDC_ENONFINITE,))
 

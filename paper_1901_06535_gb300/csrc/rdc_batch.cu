@@ -595,6 +595,13 @@ int rdc_batch_get_info(rdc_batch* b, rdc_batch_info* out)
     return RDC_OK;
 }
 
+int rdc_batch_get_grid(rdc_batch* b, int32_t idx, rdc_grid* out)
+{
+    if (!b || !out || idx < 0 || idx >= b->n || !b->mem[idx]) return RDC_EINVAL;
+    *out = b->grids[idx];
+    return RDC_OK;
+}
+
 int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
 {
     if (!b || reps < 1) return RDC_EINVAL;

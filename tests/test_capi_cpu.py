@@ -207,3 +207,45 @@ def test_noalloc_scratch_limit_is_exact(librdc):
                                 fake + 8192, fake + 12288, fake + 16384, w * esz, 3, None,
                                 None)
         assert rc == librdc.RDC_EUNSUPPORTED, (prec, rc)
+
+
+def test_binding_checks_host_array_sizes(monkeypatch):
+    """Host arrays passed to the library must hold one value per cell (the
+    library reads or writes exactly width * height of them) and u and v the
+    same dtype: the binding refuses anything else before calling the library
+    (here a fake grid of 8 x 4 cells; the library is never reached)."""
+    import numpy as np
+    from paper_1901_06535_gb300 import _capi
+
+    def no_lib():
+        raise AssertionError("the library must not be called")
+
+    monkeypatch.setattr(_capi, "lib", no_lib)
+    monkeypatch.setattr(_capi, "rdc_get_view",
+                        lambda h: _capi.rdc_view(width=8, height=4))
+    monkeypatch.setattr(_capi, "rdc_batch_get_grid", lambda b, idx: (8, 4))
+    good = np.zeros((4, 8))
+    for bad in (np.zeros((4, 7)), np.zeros((3, 8)), np.zeros(33), np.zeros((8, 5))):
+        for call in (lambda a: _capi.rdc_read(1, a, None),
+                     lambda a: _capi.rdc_read(1, good, a),
+                     lambda a: _capi.rdc_set_state(1, a, None),
+                     lambda a: _capi.rdc_set_phi(1, a.astype(np.float32)),
+                     lambda a: _capi.rdc_batch_read(1, 0, a, None),
+                     lambda a: _capi.rdc_batch_set_state(1, 0, good, a)):
+            with pytest.raises(ValueError, match="cells"):
+                call(bad)
+    for call in (lambda: _capi.rdc_read(1, good, good.astype(np.float32)),
+                 lambda: _capi.rdc_batch_read(1, 0, good, good.astype(np.float32)),
+                 lambda: _capi.rdc_batch_set_state(1, 0, good.astype(np.float16), good)):
+        with pytest.raises(ValueError, match="same dtype"):
+            call()
+
+
+def test_batch_get_grid_validates(librdc):
+    """rdc_batch_get_grid refuses a NULL batch or output (host only)."""
+    import ctypes
+    from paper_1901_06535_gb300._capi import rdc_grid
+    L = librdc.lib()
+    g = rdc_grid()
+    assert L.rdc_batch_get_grid(None, 0, ctypes.byref(g)) == librdc.RDC_EINVAL
+    assert L.rdc_batch_get_grid(None, 0, None) == librdc.RDC_EINVAL
