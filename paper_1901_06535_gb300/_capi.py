@@ -400,9 +400,10 @@ def rdc_check(h):
 
 
 def rdc_probe(h, cells) -> np.ndarray:
-    c = np.ascontiguousarray(cells, dtype=np.int64)
-    out = np.empty(len(c), dtype=np.float64)
-    _chk(lib().rdc_probe(h, len(c), c.ctypes.data, out.ctypes.data), "rdc_probe")
+    """u at the given flat cell indices (any shape), as a flat float64 array."""
+    c = np.ascontiguousarray(cells, dtype=np.int64).ravel()
+    out = np.empty(c.size, dtype=np.float64)
+    _chk(lib().rdc_probe(h, c.size, c.ctypes.data, out.ctypes.data), "rdc_probe")
     return out
 
 
@@ -514,7 +515,18 @@ def rdc_render(h, what: int = RDC_RENDER_SNAPSHOT, u_scale: float = 1.0, v_scale
     if out is None:
         out = np.empty((view.height, view.width, 4), dtype=np.uint8)
     on_dev = 1 if (hasattr(out, "is_cuda") and out.is_cuda) else 0
-    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    if hasattr(out, "data_ptr"):                       # torch tensor, host or device
+        ok = out.is_contiguous()
+        nbytes = out.numel() * out.element_size()
+        ptr = out.data_ptr()
+    else:
+        out = np.asarray(out)
+        ok = out.flags.c_contiguous
+        nbytes = out.nbytes
+        ptr = out.ctypes.data
+    if not ok or nbytes != view.width * view.height * 4:
+        raise ValueError(f"out: must be a contiguous buffer of {view.height} x {view.width} "
+                         f"x 4 bytes, got {nbytes} bytes")
     _chk(lib().rdc_render(h, int(what), float(u_scale), float(v_scale), float(phi_threshold),
                           ptr, on_dev), "rdc_render")
     return out

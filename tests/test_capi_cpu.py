@@ -249,3 +249,30 @@ def test_batch_get_grid_validates(librdc):
     g = rdc_grid()
     assert L.rdc_batch_get_grid(None, 0, ctypes.byref(g)) == librdc.RDC_EINVAL
     assert L.rdc_batch_get_grid(None, 0, None) == librdc.RDC_EINVAL
+
+
+def test_binding_checks_render_and_probe_buffers(monkeypatch):
+    """rdc_render's caller-supplied output must be one contiguous RGBA8 image
+    of the grid (W * H * 4 bytes); rdc_probe counts every index of a
+    multi-dimensional index array (fake 8 x 4 grid; the library is only
+    reached by the probe, through a fake that records the count)."""
+    import numpy as np
+    from paper_1901_06535_gb300 import _capi
+    monkeypatch.setattr(_capi, "rdc_get_view", lambda h: _capi.rdc_view(width=8, height=4))
+    seen = {}
+
+    class FakeLib:
+        def rdc_render(self, *a):
+            raise AssertionError("an invalid output buffer reached the library")
+
+        def rdc_probe(self, h, n, cells, out):
+            seen["n"] = n
+            return _capi.RDC_OK
+
+    monkeypatch.setattr(_capi, "lib", lambda: FakeLib())
+    for bad in (np.zeros((4, 8, 3), np.uint8), np.zeros((4, 7, 4), np.uint8),
+                np.zeros((4, 8, 4), np.uint8)[:, ::2], np.zeros((4, 8, 4), np.uint16)):
+        with pytest.raises(ValueError, match="out"):
+            _capi.rdc_render(1, out=bad)
+    out = _capi.rdc_probe(1, np.arange(12).reshape(3, 4))
+    assert seen["n"] == 12 and out.shape == (12,)
