@@ -276,3 +276,32 @@ def test_binding_checks_render_and_probe_buffers(monkeypatch):
             _capi.rdc_render(1, out=bad)
     out = _capi.rdc_probe(1, np.arange(12).reshape(3, 4))
     assert seen["n"] == 12 and out.shape == (12,)
+
+
+def test_unusable_device_is_reported_not_hidden(librdc):
+    """With no usable CUDA device (this machine), every call that needs one
+    returns RDC_ECUDA with the runtime's message in rdc_last_error and no
+    handle -- there is no CPU fallback -- and the library keeps answering
+    host-only calls afterwards."""
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a usable GPU")
+    from paper_1901_06535_gb300._capi import rdc_grid
+    L = librdc.lib()
+    p = librdc.rdc_params_default()
+    h = ctypes.c_void_p()
+    assert L.rdc_create(rdc_grid(16, 16), ctypes.byref(p), None, None,
+                        ctypes.byref(h)) == librdc.RDC_ECUDA
+    assert h.value is None and librdc.rdc_last_error().startswith("cudaGetDevice")
+    b = ctypes.c_void_p()
+    assert L.rdc_batch_create(0, None, ctypes.byref(p), None, None,
+                              ctypes.byref(b)) == librdc.RDC_ECUDA and b.value is None
+    rep = librdc.rdc_division_report()
+    assert L.rdc_check_division(0.002, 0, 0, ctypes.byref(rep)) == librdc.RDC_ECUDA
+    # host-only calls still work, and validation still comes first
+    assert librdc.rdc_rest_state(0.054, 1.4, 0.002) > 0.002
+    bad = librdc.rdc_params_default()
+    bad.dt = -1.0
+    assert L.rdc_create(rdc_grid(16, 16), ctypes.byref(bad), None, None,
+                        ctypes.byref(h)) == librdc.RDC_EINVAL
