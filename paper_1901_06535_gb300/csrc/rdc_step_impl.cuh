@@ -205,8 +205,9 @@ __device__ __forceinline__ Model<T> model_of(const GridDesc& d)
     return m;
 }
 
-// Persistent single step over a batch of grids: every warp takes items
-// w, w + (all warps), ...; each item is one warp's strip of one grid.
+// Persistent single step over a batch of grids: every warp takes items from
+// the work queue until the list is exhausted; each item is one warp's strip
+// of one grid.
 template <typename S, int MODE>
 __global__ void __launch_bounds__(128)
 k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
