@@ -311,6 +311,18 @@ def pin_render(o, om):
     assert np.array_equal(tl, np.maximum(np.maximum(u, 0), 0.75).astype(np.float32))
     img = o.render(u, v, phi, 1.0, 1.0, thr=0.07575, tl=tl)
     assert (img[..., 2] == 0).all() and img[0, 1, 0] == 191   # 0.75 * 255 = 191.25
+    # green where phi >= the threshold: at it, and one double either side
+    t = 0.07575
+    z = np.zeros((1, 3), dtype=np.float32)
+    img = o.render(z, z, np.array([[t, np.nextafter(t, 0.0), np.nextafter(t, 1.0)]]), thr=t)
+    assert img[0, :, 1].tolist() == [255, 0, 255]
+    # a reset replaces the record whatever it held (larger values included)
+    import ctypes
+    fp = ctypes.POINTER(ctypes.c_float)
+    rec = np.full(u.shape, 5.0, dtype=np.float32)
+    uu = np.ascontiguousarray(u, dtype=np.float32)
+    o.lib.orc_timelapse(uu.size, uu.ctypes.data_as(fp), rec.ctypes.data_as(fp), 1)
+    assert np.array_equal(rec, uu)
 
 
 def pin_draw(o, om):
@@ -323,6 +335,7 @@ def pin_draw(o, om):
         rows = np.nonzero(phi[:, 17])[0]
         assert len(rows) == width, (width, rows)
         assert phi[:, :5 - width // 2 - 1].sum() == 0        # ends are rounded caps
+        assert phi[:, 30 + width // 2 + 2:].sum() == 0       # the segment ends at x1
     x1, y1 = o.snap_segment(0.0, 0.0, 10.0, 9.4, 15.0)     # 43.2 deg -> 45
     assert abs(x1 - y1) < 1e-12 and abs(np.hypot(x1, y1) - np.hypot(10.0, 9.4)) < 1e-12
     x1, y1 = o.snap_segment(3.0, 4.0, 20.0, 5.0, 15.0)     # 3.4 deg -> 0
@@ -395,7 +408,43 @@ def pin_philox(o, om):
     assert float(((counts - exp) ** 2 / exp).sum()) < 350.0
 
 
+def pin_round_stoch_cells(o, om):
+    """The rounding of a row of cells: with x exactly halfway between two
+    BF16 values each draw is a fair coin, so the patterns show that every
+    field of the counter (the quad column / 4, the row, both halves of the
+    64-bit step) and the key changes the draws, that u and v use different
+    bits, that the four cells of a quad use four different words, that a
+    cell's bits do not depend on where the row segment starts, and that the
+    rounding is unbiased over steps.  (Which bits go to u and which to v is a
+    convention the GPU parity test fixes.)"""
+    base = int(np.float32(0.3).view(np.uint32)) & 0xFFFF0000
+    x0 = np.uint32(base | 0x8000).view(np.float32)            # halfway
+    lo = float(np.uint32(base).view(np.float32))
+    hi = float(np.uint32(base + 0x10000).view(np.float32))
+    x = np.full(64, x0, dtype=np.float32)
+
+    def pattern(seed=5, step=7, row=3, col0=0, n=64):
+        u, v = o.round_stoch_cells(x[:n], seed, step, row, col0, "bf16")
+        assert set(np.unique(u)) <= {lo, hi} and set(np.unique(v)) <= {lo, hi}
+        return u == hi, v == hi
+
+    bu, bv = pattern()
+    assert 10 < bu.sum() < 54 and 10 < bv.sum() < 54, (bu.sum(), bv.sum())
+    assert not np.array_equal(bu, bv)
+    for kw in ({"seed": 6}, {"step": 8}, {"step": 7 + 2 ** 32}, {"row": 4}):
+        assert not np.array_equal(pattern(**kw)[0], bu), kw
+    quads = bu.reshape(16, 4)
+    assert not all(len(set(q)) == 1 for q in quads)           # one word per cell
+    assert len({tuple(q) for q in quads}) > 4                 # one call per quad
+    su, _ = pattern(col0=4, n=60)
+    assert np.array_equal(su, bu[4:])
+    draws = [o.round_stoch_cells(x[:1], 5, s, 3, 0, "bf16")[0][0] for s in range(4000)]
+    sd = (hi - lo) / 2 / math.sqrt(len(draws))
+    assert abs(float(np.mean(draws)) - float(x0)) < 5 * sd
+
+
 ALL_PINS = [pin_rest_root, pin_rest_fixed_point, pin_jacobian, pin_jacobian_with_mode,
             pin_cosine_modes,
             pin_conservation, pin_symmetry, pin_one_d, pin_uniform_is_single, pin_spike,
-            pin_gauss_circle, pin_health, pin_render, pin_draw, pin_round_stoch, pin_philox]
+            pin_gauss_circle, pin_health, pin_render, pin_draw, pin_round_stoch, pin_philox,
+            pin_round_stoch_cells]
