@@ -15,16 +15,22 @@ Parity status of the functions (what pins each one is in ``tests/``):
                                 analytic Jacobian, symmetries, 1-D reduction,
                                 AND-gate and diode behaviour of §4)
   * seed_disk                -- pinned (Gauss circle counts)
-  * draw_line / snap_segment -- pinned (line widths of the §3 presets, snapped
-                                angles and preserved length)
+  * draw_line / snap_segment -- pinned (line widths of the §3 presets, end
+                                caps, snapped angles and preserved length)
   * render / timelapse       -- pinned (channel assignment of §3.1, clamping,
-                                round-half-even codes, running maximum)
+                                round-half-even codes, the green threshold's
+                                edge, running maximum and its reset)
   * arrival times in run     -- parity unpinned: the paper prints no wave
                                 speeds or arrival times; only the
                                 interpolation rule itself is checked.
   * round_stoch              -- pinned (exact unbiasedness over all 2^16
                                 random values, both neighbours on the target
                                 grid, round-to-nearest cases)
+  * round_stoch_cells        -- pinned by properties (every counter field and
+                                the key change the draws, u and v and the
+                                cells of a quad draw different bits, position
+                                independence, unbiasedness over steps); which
+                                half-word goes to u is a convention
   * philox4x32_10            -- partly pinned: bijectivity in each counter
                                 word, avalanche and uniformity of the output
                                 bits; no published output values are used.
