@@ -10,6 +10,8 @@ Workload (one bench step = one pass of the whole hot path over one input):
 The JSON line also reports temporal blocking (k steps per launch) and the
 reduced-storage modes as effective GCUPS on the same grid, the end-to-end
 rate through the C ABI with host buffers (phi in, state out, every step),
+the 512-grid parameter sweep (batched kernels, one CUDA graph), the
+64-session serving workload (p50/p99 frame latency), the colour map's rate,
 and the FP64 oracle timed on the host cores as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
