@@ -20,9 +20,11 @@ Parity status of the functions (what pins each one is in ``tests/``):
   * render / timelapse       -- pinned (channel assignment of §3.1, clamping,
                                 round-half-even codes, the green threshold's
                                 edge, running maximum and its reset)
-  * arrival times in run     -- parity unpinned: the paper prints no wave
-                                speeds or arrival times; only the
-                                interpolation rule itself is checked.
+  * arrival times in run     -- pinned by brute force (the recorded crossing
+                                of theta and its linear interpolation equal
+                                those of separate runs to the two steps
+                                around it); the paper prints no wave speeds or
+                                arrival times to compare the values with.
   * round_stoch              -- pinned (exact unbiasedness over all 2^16
                                 random values, both neighbours on the target
                                 grid, round-to-nearest cases)
@@ -31,9 +33,10 @@ Parity status of the functions (what pins each one is in ``tests/``):
                                 cells of a quad draw different bits, position
                                 independence, unbiasedness over steps); which
                                 half-word goes to u is a convention
-  * philox4x32_10            -- partly pinned: bijectivity in each counter
+  * philox4x32_10            -- pinned (the published known-answer vectors
+                                of Philox4x32-10; bijectivity in each counter
                                 word, avalanche and uniformity of the output
-                                bits; no published output values are used.
+                                bits)
 """
 from __future__ import annotations
 

@@ -32,9 +32,11 @@ What each pin fixes:
                        values the mean is exactly x; the results are the two
                        grid neighbours (NumPy float16, bit truncation for
                        BF16) split at the stated threshold.
-  philox               Philox4x32-10 is a bijection in each counter word, every
-                       input bit flips about half the output bits, the output
-                       is uniform (no published output values are used).
+  philox               Philox4x32-10 reproduces the generator's published
+                       known-answer vectors (tests/golden/philox4x32_10_kat.txt:
+                       Random123's entries for 10 rounds); besides, it is a
+                       bijection in each counter word, every input bit flips
+                       about half the output bits, the output is uniform.
   symmetry             a seed invariant under the 8 symmetries of the square
                        stays exactly invariant.
   one_d                rows that are identical stay identical and equal the
@@ -51,6 +53,7 @@ What each pin fixes:
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -377,7 +380,27 @@ def pin_round_stoch(o, om):
     assert o.round_stoch(65520.0, 65535, "f16") == float("inf")
 
 
+def philox_kat():
+    """(counter, key, output) triples of the published known-answer vectors."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "philox4x32_10_kat.txt")
+    out = []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(x, 16) for x in line.split()]
+            assert len(w) == 10, line
+            out.append((w[0:4], w[4:6], w[6:10]))
+    return out
+
+
 def pin_philox(o, om):
+    kat = philox_kat()
+    assert len(kat) == 3
+    for ctr, key, want in kat:
+        got = [int(x) for x in o.philox4x32_10(ctr, key)]
+        assert got == want, (ctr, key, [hex(x) for x in got])
     key = [0x1234567, 0x89ABCDE]
     for word in range(4):
         outs = set()

@@ -48,6 +48,12 @@ MUTANTS = [
     ("philox_key_dropped", "^ c[1] ^ k0;", "^ c[1];"),
     ("philox_one_round", "round < 10; ++round", "round < 1; ++round"),
     ("philox_word_reused", "^ c[3] ^ k1;", "^ c[1] ^ k1;"),
+    ("philox_wrong_multiplier", "0xD2511F53u * (uint64_t)c[0]", "0xD2511F55u * (uint64_t)c[0]"),
+    ("philox_hi_lo_swapped",
+     "const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;\n        const uint32_t n3 = (uint32_t)p0;",
+     "const uint32_t n2 = (uint32_t)p0 ^ c[3] ^ k1;\n        const uint32_t n3 = (uint32_t)(p0 >> 32);"),
+    ("philox_key_bumped_first", "uint32_t k0 = key[0], k1 = key[1];",
+     "uint32_t k0 = key[0] + 0x9E3779B9u, k1 = key[1] + 0xBB67AE85u;"),
     ("render_red_from_v", "out[4 * k + 0] = r;", "out[4 * k + 0] = b;"),
     ("render_green_strict", "(phi[k] >= thr) ? 255 : 0", "(phi[k] > thr) ? 255 : 0"),
     ("render_no_upper_clamp", "if (y > 1.0f) y = 1.0f;", ""),

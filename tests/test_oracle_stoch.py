@@ -6,11 +6,12 @@ the mean result is exactly x (unbiasedness), the two possible results are the
 neighbours of x on the target grid (checked against NumPy's float16 and a
 bit truncation for bfloat16), the probability of rounding away from zero
 grows with the distance to the lower neighbour, and the round-to-nearest
-cases.  Philox has no published value used here; it is pinned by properties
-its definition implies: each round is a bijection of the counter for a fixed
-key (so distinct counters give distinct outputs), every input bit affects
-about half of the output bits after ten rounds, and the output words are
-uniform."""
+cases.  Philox is pinned by the generator's published known-answer vectors
+(tests/golden/philox4x32_10_kat.txt, checked in tests/oracle_pins.py) and by
+properties its definition implies: each round is a bijection of the counter
+for a fixed key (so distinct counters give distinct outputs), every input bit
+affects about half of the output bits after ten rounds, and the output words
+are uniform."""
 from __future__ import annotations
 
 from fractions import Fraction
