@@ -613,6 +613,18 @@ int rdc_stoch_round_sample(int32_t precision, uint32_t seed, int64_t step, int32
                            int32_t col0, int32_t n, const float* x, float* u_out,
                            float* v_out);
 
+/*
+ * The paper has no counterpart: exposes the Philox4x32-10 generator (Salmon
+ * et al., SC'11) whose words drive RDC_STOCH_ROUND, so that it can be checked
+ * against the generator's published known-answer vectors.  For i in 0..n-1,
+ * out[4i .. 4i+3] receives the four output words for counter ctr[4i .. 4i+3]
+ * and key key[2i], key[2i+1], computed on the current device by the function
+ * the step kernels call.  Host arrays (copied).  Synchronous; allocates and
+ * frees device memory.  RDC_EINVAL: n < 0, n > 2^24, or a NULL array with
+ * n > 0.
+ */
+int rdc_philox_sample(int32_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+
 /* Human-readable name of a status code (static storage). */
 const char* rdc_status_str(int status);
 

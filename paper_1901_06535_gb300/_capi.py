@@ -173,6 +173,7 @@ _SIGS = {
     "rdc_stoch_round_sample": (ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64,
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               _P, _P, _P]),
+    "rdc_philox_sample": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P]),
     "rdc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "rdc_last_error": (ctypes.c_char_p, []),
 }
@@ -454,6 +455,20 @@ def rdc_stoch_round_sample(precision, seed: int, step: int, row: int, col0: int,
                                       x.ctypes.data, u.ctypes.data, v.ctypes.data),
          "rdc_stoch_round_sample")
     return u, v
+
+
+def rdc_philox_sample(ctr, key):
+    """Philox4x32-10 on the device, as the step kernels compute it: ctr is an
+    (n, 4) array of counters, key an (n, 2) array of keys (32-bit words);
+    returns the (n, 4) uint32 outputs."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    if c.shape[0] != k.shape[0]:
+        raise ValueError("one key per counter")
+    out = np.empty_like(c)
+    _chk(lib().rdc_philox_sample(int(c.shape[0]), c.ctypes.data, k.ctypes.data,
+                                 out.ctypes.data), "rdc_philox_sample")
+    return out
 
 
 def rdc_step_noalloc(width: int, height: int, params: rdc_params, u_in: int, v_in: int,

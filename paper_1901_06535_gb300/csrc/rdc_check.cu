@@ -1,6 +1,7 @@
 // Diagnostics of the step kernels' arithmetic: rdc_check_division checks
 // the FP32 division exhaustively, rdc_stoch_round_sample exposes the
-// stochastic rounding of RDC_STOCH_ROUND.
+// stochastic rounding of RDC_STOCH_ROUND and rdc_philox_sample the
+// Philox4x32-10 generator behind it.
 //
 // rdc_check_division: exhaustive device check of the FP32 division that
 // every FP32 step kernel uses for the ratio (u - q)/(u + q) of Eq. 1.
@@ -147,10 +148,56 @@ __global__ void k_sr_sample(const float* __restrict__ x, int n, unsigned seed, l
     vo[i] = quantize_sr<S>(x[i], w << 16);
 }
 
+// Philox4x32-10 outputs for n given counters and keys, computed by the very
+// function the stochastically rounding step kernels call.
+__global__ void k_philox_sample(const unsigned* __restrict__ ctr,
+                                const unsigned* __restrict__ key, int n,
+                                unsigned* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Philox4 c{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    const Philox4 r = philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
 }  // namespace
 }  // namespace rdc
 
 using namespace rdc;
+
+extern "C" int rdc_philox_sample(int32_t n, const uint32_t* ctr, const uint32_t* key,
+                                 uint32_t* out)
+{
+    if (n < 0 || n > (1 << 24) || (n > 0 && (!ctr || !key || !out))) return RDC_EINVAL;
+    if (n == 0) return RDC_OK;
+    int rc = host_check_device();
+    if (rc) return rc;
+    unsigned* d = nullptr;
+    const size_t words = (size_t)n * 10;  // 4 counter, 2 key, 4 output words each
+    cudaError_t e = cudaMalloc((void**)&d, words * sizeof(unsigned));
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(philox sample)");
+    unsigned* dc = d;
+    unsigned* dk = d + 4 * (size_t)n;
+    unsigned* dout = d + 6 * (size_t)n;
+    do {
+        if ((e = cudaMemcpy(dc, ctr, 4 * (size_t)n * sizeof(unsigned),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            break;
+        if ((e = cudaMemcpy(dk, key, 2 * (size_t)n * sizeof(unsigned),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            break;
+        const int bs = 256, gs = (n + bs - 1) / bs;
+        k_philox_sample<<<gs, bs>>>(dc, dk, n, dout);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        e = cudaMemcpy(out, dout, 4 * (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToHost);
+    } while (false);
+    cudaFree(d);
+    return e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "philox sample");
+}
 
 extern "C" int rdc_stoch_round_sample(int32_t precision, uint32_t seed, int64_t step,
                                       int32_t row, int32_t col0, int32_t n, const float* x,

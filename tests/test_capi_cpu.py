@@ -150,6 +150,17 @@ def test_stoch_round_sample_validates_before_touching_the_device(librdc):
         assert e.value.status == librdc.RDC_EINVAL
 
 
+def test_philox_sample_validates_before_touching_the_device(librdc):
+    import ctypes
+    lib = librdc.lib()
+    buf = (ctypes.c_uint32 * 8)()
+    assert lib.rdc_philox_sample(-1, buf, buf, buf) == librdc.RDC_EINVAL
+    assert lib.rdc_philox_sample((1 << 24) + 1, buf, buf, buf) == librdc.RDC_EINVAL
+    assert lib.rdc_philox_sample(1, None, buf, buf) == librdc.RDC_EINVAL
+    assert lib.rdc_philox_sample(1, buf, buf, None) == librdc.RDC_EINVAL
+    assert lib.rdc_philox_sample(0, None, None, None) == librdc.RDC_OK
+
+
 def test_params_reject_unknown_fields(librdc):
     with pytest.raises(TypeError):
         librdc.rdc_params_default(reserved=0)

@@ -1,5 +1,7 @@
 """Stochastic rounding to 16-bit storage (RDC_STOCH_ROUND) on the GPU.
 
+* The device's Philox4x32-10 reproduces the generator's published
+  known-answer vectors and equals the oracle's on random counters and keys.
 * The device rounding of a value, for any cell, step and key, equals the
   oracle's (its own Philox4x32-10 and rounding rule, written separately),
   bit for bit.
@@ -28,6 +30,22 @@ def _values(rng, n):
     x = mag * rng.choice(np.array([-1, 1], dtype=np.float32), n)
     x[:8] = [0.0, -0.0, 0.3, 0.5, 65504.0, 65510.0, 1e-7, -2.5e-5]
     return x
+
+
+def test_device_philox_known_answers(gpu, orc):
+    from tests.oracle_pins import philox_kat
+    kat = philox_kat()
+    ctr = np.array([c for c, _, _ in kat], dtype=np.uint32)
+    key = np.array([k for _, k, _ in kat], dtype=np.uint32)
+    want = np.array([o for _, _, o in kat], dtype=np.uint32)
+    assert np.array_equal(gpu.rdc_philox_sample(ctr, key), want)
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2**32, (4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, (4096, 2), dtype=np.uint64).astype(np.uint32)
+    got = gpu.rdc_philox_sample(ctr, key)
+    ref = np.array([orc.philox4x32_10([int(x) for x in c], [int(x) for x in k])
+                    for c, k in zip(ctr, key)], dtype=np.uint32)
+    assert np.array_equal(got, ref)
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "f16"])
