@@ -424,17 +424,22 @@ int rdc_set_shape(rdc_sim* sim, const rdc_launch_shape* in);
  * deployment convenience).  Advances caller-owned device buffers by n >= 0
  * Euler steps, exactly as rdc_step would (same kernels, same bits), and
  * allocates no device memory: no cudaMalloc, no cudaFree, no allocating
- * library call.  For callers that cannot allocate -- code running while a
- * stream is being captured into a CUDA graph, hosts whose device memory comes
- * from their own pool, loops where cudaMalloc's implicit device
- * synchronisation is not acceptable.
- *   g, p           : as rdc_create (p->k_block selects temporal blocking);
+ * library call.  For callers that cannot allocate: applications whose device
+ * memory is handed out by their own pool (a framework's caching allocator
+ * that has reserved the device), where a library's allocation could fail or
+ * fragment that pool; latency-bound loops, where cudaMalloc and cudaFree
+ * would synchronise the device and stall every other stream's work; and
+ * processes that must know their device footprint up front.
+ *   g, p           : as rdc_create (p->k_block selects temporal blocking;
+ *                    RDC_STOCH_ROUND is refused: no step index is kept);
  *   u_in, v_in     : current state, storage type of p->precision, never
  *                    written;
  *   phi            : phi map (float; double for RDC_F64) with the same pitch
  *                    in elements as the state planes;
- *   u_out, v_out   : receive the state after n steps (distinct from the
- *                    inputs);
+ *   u_out, v_out   : receive the state after n steps; neither may share a
+ *                    byte with any other buffer of the call (each state plane
+ *                    taken as pitch_bytes * H bytes, phi as the same rows of
+ *                    its elements), else RDC_EINVAL;
  *   pitch_bytes    : row stride of the state planes, a multiple of 16 and of
  *                    the element size, >= W * element size; all pointers
  *                    16-byte aligned;
@@ -444,17 +449,20 @@ int rdc_set_shape(rdc_sim* sim, const rdc_launch_shape* in);
  *                    rdc_check on u_out, synchronises the stream, stores the
  *                    first bad flat index (or -1) and returns
  *                    RDC_ENONFINITE if one exists.
- * Scratch: intermediate states of multi-step calls and the health flag live
- * in one file-scope device array of 32 MiB that every GPU loading this
- * library holds until the process exits.  A grid needs 256 + 2 *
- * roundup256(pitch_bytes * H) bytes of it (FP32: just under 4 M cells, e.g.
- * 2048 x 2047; 2048 x 2048 is 256 bytes over); larger grids get
- * RDC_EUNSUPPORTED before anything is enqueued.  The first call on each device looks the array's address up
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the array and it keeps the
- * previous call's contents (the flag is reset on every call): calls whose
- * work overlaps on the GPU -- on different streams or different threads --
- * race on it and must be serialised by the caller.
+ * Scratch: the call makes n / k + n % k launches (n with k_block <= 1).  With
+ * two or more, the intermediate states live in one file-scope device array
+ * of 32 MiB that every GPU loading this library holds until the process
+ * exits; such a call needs 256 + 2 * roundup256(pitch_bytes * H) bytes of it
+ * (FP32: just under 4 M cells, e.g. 2048 x 2047; 2048 x 2048 is 256 bytes
+ * over) and larger grids get RDC_EUNSUPPORTED before anything is enqueued.
+ * Calls of at most one launch use no scratch plane and take grids of any
+ * size; the health check uses 8 bytes of the array.  The first call on each
+ * device that uses the array looks its address up (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream
+ * capture.  Every call shares the array and it keeps the previous call's
+ * contents (the flag is reset on every call): calls whose work overlaps on
+ * the GPU -- on different streams or different threads -- race on it and
+ * must be serialised by the caller.
  */
 int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_in,
                      const void* v_in, const void* phi, void* u_out, void* v_out,

@@ -1,13 +1,15 @@
 // rdc_step_noalloc: advance caller-owned state buffers by n Euler steps
 // without any device allocation.
 //
-// Who needs it: callers that cannot call cudaMalloc -- code that runs while
-// a stream is being captured into a CUDA graph (allocation is not allowed
-// there), hosts whose device memory is handed out by their own pool and must
-// not be touched by a library, and latency-bound loops where cudaMalloc's
-// implicit device synchronisation is not acceptable.  The simulation handle
-// API allocates its planes and a small scratch area; this entry point takes
-// every input and output from the caller instead.
+// Who needs it: callers that cannot call cudaMalloc -- applications whose
+// device memory is handed out by their own pool (a framework's caching
+// allocator that has reserved the device), where a library's own allocation
+// could fail or fragment that pool; latency-bound loops (interactive serving)
+// where cudaMalloc and cudaFree would synchronise the device and stall the
+// work of every other stream; and processes that must know their device
+// footprint up front.  The simulation handle API allocates its planes and a
+// small scratch area; this entry point takes every input and output from the
+// caller instead.
 //
 // The only memory it uses beyond the caller's buffers is g_scratch below: a
 // file-scope device array of a fixed size that every GPU loading this
@@ -75,6 +77,13 @@ bool params_ok(const rdc_params* p)
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
+// Whether the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
 
 }  // namespace
 
@@ -89,23 +98,40 @@ extern "C" int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_i
     const void* ptrs[5] = {u_in, v_in, phi, u_out, v_out};
     for (const void* q : ptrs)
         if (!q || ((uintptr_t)q % 16)) return RDC_EINVAL;
-    if (u_out == u_in || v_out == v_in || u_out == v_out) return RDC_EINVAL;
     const int prec = p->precision;
     const size_t esz = (size_t)state_bytes(prec);
     if (pitch_bytes % 16 || pitch_bytes % esz || pitch_bytes < (size_t)g.width * esz)
         return RDC_EINVAL;
-    const size_t plane = round256(pitch_bytes * (size_t)g.height);
-    // Grids whose two scratch planes do not fit the static array are
+    // The kernels read their inputs through restrict-qualified pointers and
+    // write whole output planes, so an output that shares any byte with
+    // another buffer would give wrong states: refuse it.  Each state plane
+    // spans pitch_bytes * H bytes, phi the same rows at its own element size.
+    const size_t sbytes = pitch_bytes * (size_t)g.height;
+    const size_t pbytes = pitch_bytes / esz * (prec == P_F64 ? 8 : 4) * (size_t)g.height;
+    if (overlap(u_out, sbytes, v_out, sbytes)) return RDC_EINVAL;
+    for (void* o : {u_out, v_out})
+        if (overlap(o, sbytes, u_in, sbytes) || overlap(o, sbytes, v_in, sbytes) ||
+            overlap(o, sbytes, phi, pbytes))
+            return RDC_EINVAL;
+    const int k = p->k_block == 0 ? 1 : p->k_block;
+    // Launches: n / k of the k-step kernel and n % k single steps.  Only
+    // calls of two or more launches keep an intermediate state in the
+    // scratch array; those whose two scratch planes do not fit it are
     // refused before anything is enqueued.
-    if (kFlagBytes + 2 * plane > kScratchBytes) return RDC_EUNSUPPORTED;
+    const int64_t L = (k > 1) ? n / k + n % k : n;
+    const size_t plane = round256(sbytes);
+    if (L >= 2 && kFlagBytes + 2 * plane > kScratchBytes) return RDC_EUNSUPPORTED;
 
-    void* base = nullptr;
-    int rc = scratch_address(&base);
-    if (rc) return rc;
-    unsigned char* b = static_cast<unsigned char*>(base);
+    unsigned char* b = nullptr;
+    if (L >= 2 || first_bad) {
+        void* base = nullptr;
+        int rc = scratch_address(&base);
+        if (rc) return rc;
+        b = static_cast<unsigned char*>(base);
+    }
     unsigned long long* flag = reinterpret_cast<unsigned long long*>(b);
-    void* su = b + kFlagBytes;
-    void* sv = b + kFlagBytes + plane;
+    void* su = L >= 2 ? b + kFlagBytes : nullptr;
+    void* sv = L >= 2 ? b + kFlagBytes + plane : nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t pitch = (int64_t)(pitch_bytes / esz);
 
@@ -116,7 +142,6 @@ extern "C" int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_i
     m.Du = p->Du;
     m.dt = p->dt;
     m.inv_dx2 = 1.0 / (p->dx * p->dx);
-    const int k = p->k_block == 0 ? 1 : p->k_block;
 
     // Launch shapes: the library's defaults for a grid of this size.  (Any
     // valid shape gives the same bits.)
@@ -141,7 +166,6 @@ extern "C" int rdc_step_noalloc(rdc_grid g, const rdc_params* p, const void* u_i
     } else {
         // Launch j of L writes the output buffers when L - j is even and the
         // scratch pair otherwise, so the last launch lands in the output.
-        const int64_t L = (k > 1) ? n / k + n % k : n;
         const void* cu = u_in;
         const void* cv = v_in;
         int64_t left = n;

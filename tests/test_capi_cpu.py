@@ -212,12 +212,46 @@ def test_noalloc_scratch_limit_is_exact(librdc):
     L = librdc.lib()
     from paper_1901_06535_gb300._capi import rdc_grid
     fake = 1 << 40
+    gap = 1 << 26                                       # 64 MiB apart: no overlap
     for prec, (w, h), esz in ((0, (2048, 2048), 4), (2, (4096, 2048), 2), (1, (1024, 2048), 8)):
-        p = librdc.rdc_params_default(precision=prec)
-        rc = L.rdc_step_noalloc(rdc_grid(w, h), ctypes.byref(p), fake, fake + 4096,
-                                fake + 8192, fake + 12288, fake + 16384, w * esz, 3, None,
-                                None)
-        assert rc == librdc.RDC_EUNSUPPORTED, (prec, rc)
+        for kb, n in ((0, 3), (4, 5), (4, 8)):          # 3, 2 and 2 launches
+            p = librdc.rdc_params_default(precision=prec, k_block=kb)
+            rc = L.rdc_step_noalloc(rdc_grid(w, h), ctypes.byref(p), fake, fake + gap,
+                                    fake + 2 * gap, fake + 3 * gap, fake + 4 * gap, w * esz,
+                                    n, None, None)
+            assert rc == librdc.RDC_EUNSUPPORTED, (prec, kb, n, rc)
+
+
+def test_noalloc_refuses_outputs_that_overlap_another_buffer(librdc):
+    """An output plane sharing any byte with another buffer of the call would
+    be read through a restrict pointer while written: refused with RDC_EINVAL
+    before any device call (fake, never dereferenced addresses)."""
+    import ctypes
+    L = librdc.lib()
+    from paper_1901_06535_gb300._capi import rdc_grid
+    W, H, pitch = 16, 16, 64                            # planes of 1024 bytes (FP32)
+    fake = 1 << 40
+    ui, vi, ph, uo, vo = (fake + i * 4096 for i in range(5))
+    cases = {
+        "v_out is u_in": (ui, vi, ph, uo, ui),
+        "u_out is v_in": (ui, vi, ph, vi, vo),
+        "u_out one row into u_in": (ui, vi, ph, ui + pitch, vo),
+        "v_out ends inside u_in": (ui, vi, ph, uo, ui - 1008),
+        "phi is u_out": (ui, vi, uo, uo, vo),
+        "phi overlaps v_out": (ui, vi, vo + 512, uo, vo),
+        "u_out overlaps v_out": (ui, vi, ph, uo, uo + 1008),
+    }
+    for name, (a, b, c, d, e) in cases.items():
+        p = librdc.rdc_params_default(precision=0)
+        rc = L.rdc_step_noalloc(rdc_grid(W, H), ctypes.byref(p), a, b, c, d, e, pitch, 3,
+                                None, None)
+        assert rc == librdc.RDC_EINVAL, name
+    # FP64: phi is read as doubles, so a 1024-byte state plane's phi spans 2048 bytes
+    p = librdc.rdc_params_default(precision=1)
+    pitch64 = 128
+    rc = L.rdc_step_noalloc(rdc_grid(W, H), ctypes.byref(p), fake, fake + 8192, fake + 16384,
+                            fake + 16384 + 2048 - 16, fake + 32768, pitch64, 3, None, None)
+    assert rc == librdc.RDC_EINVAL
 
 
 def test_binding_checks_host_array_sizes(monkeypatch):
