@@ -493,12 +493,40 @@ def _batch_sweep(pkg, stream, steps=5000, n_grids=512, shape=None):
         sec = a.elapsed_time(z) / 1e3
         bad = [i for i in range(len(grids)) if pkg.rdc_batch_check(b, i)[0] != 0]
         cells = float(sum(n * n for n in spec.sizes))
-        return {"gcups": cells * steps / sec / 1e9, "seconds": sec, "grids": len(grids),
-                "cells": cells, "steps": steps, "k": info.k, "rows": info.rows,
-                "krows": info.krows, "tuned_gcups": info.tuned_gcups,
-                "tune_seconds": tune_s, "unhealthy_grids": bad}
+        healthy = cells - float(sum(spec.sizes[i] ** 2 for i in bad))
     finally:
         pkg.rdc_batch_destroy(b)
+    # the grids that crossed the pole (u + q <= 0), replayed alone up to the
+    # first step whose state fails the health check (same bits as in the batch)
+    first_bad = {}
+    for i in bad:
+        first_bad[str(i)] = _first_bad_step(pkg, stream, spec, i, 2 * steps)
+    return {"gcups": cells * steps / sec / 1e9, "seconds": sec, "grids": len(grids),
+            "cells": cells, "steps": steps, "k": info.k, "rows": info.rows,
+            "krows": info.krows, "tuned_gcups": info.tuned_gcups,
+            "tune_seconds": tune_s, "unhealthy_grids": bad,
+            "gcups_healthy_grids_only": healthy * steps / sec / 1e9,
+            "first_bad": first_bad}
+
+
+def _first_bad_step(pkg, stream, spec, i, steps):
+    """Step index and flat cell of the first unhealthy state of sweep grid i
+    run alone (FP32, single steps, a health check after each), or None."""
+    n = spec.sizes[i]
+    p = pkg.rdc_params_default(precision=0, eps=spec.eps[i], k_block=1)
+    phi = np.full((n, n), spec.phi[i], dtype=np.float32)
+    h = pkg.rdc_create(n, n, p, phi, stream.cuda_stream)
+    try:
+        for (cx, cy, r) in spec.disks[i]:
+            pkg.rdc_seed(h, cx, cy, r, ri.SEED_VALUE)
+        for s in range(1, steps + 1):
+            pkg.rdc_step(h, 1)
+            rc, cell = pkg.rdc_check(h)
+            if rc != 0:
+                return {"step": s, "cell": int(cell)}
+        return None
+    finally:
+        pkg.rdc_destroy(h)
 
 
 def run_only(args):

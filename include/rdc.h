@@ -147,6 +147,11 @@ int rdc_params_default(rdc_params* out);
  *              library-owned non-blocking stream.  A caller's stream must
  *              outlive the simulation.
  *   out      : receives the handle; *out is NULL on failure.
+ * The call also records whether forward Euler is linearly unstable at the
+ * rest state of the map's largest phi (as rdc_stability computes it; phi =
+ * 0.2, the workloads' passive background, is): rdc_view's unstable and
+ * stability_rho hold the result, kept current by every call that changes
+ * phi.  rdc_create still returns RDC_OK then; the handle is usable.
  * Validation (RDC_EINVAL): W or H < 1; a non-finite parameter; eps, q, dt
  * or dx <= 0; Du < 0; f + q <= 1; Du dt / dx^2 > 1/4 (the explicit
  * diffusion limit); both test flags set; RDC_STOCH_ROUND with FP32 or FP64
@@ -173,6 +178,8 @@ int rdc_create_f64phi(rdc_grid g, const rdc_params* p, const double* phi_host,
  * All pointers must be 16-byte aligned.  The state is NOT initialised: the
  * current state is dev_u[0], dev_v[0] as the caller left it (use
  * rdc_reset_rest to set the rest state).  The library never frees them.
+ * The map's largest value (for the stability record) is found on the device;
+ * the call synchronises the stream.
  */
 int rdc_create_ext(rdc_grid g, const rdc_params* p, void* const dev_u[2],
                    void* const dev_v[2], const void* dev_phi,
@@ -353,6 +360,10 @@ int rdc_rest_state(double phi, double f, double q, double* u_star);
  * (from 0 to -8 Du / dx^2).  Returns RDC_EUNSTABLE_WARN when rho > 1 (the
  * homogeneous state then oscillates with period 2 instead of resting), else
  * RDC_OK.  (Table 1's phi_active gives rho < 1; phi = 0.2 gives rho > 1.)
+ * The largest phi is that of the map as set, filled or read at creation; a
+ * drawn line raises it when its value is larger (so after drawing it is an
+ * upper bound).  The same result is recorded in rdc_view at every change of
+ * phi.
  */
 int rdc_stability(rdc_sim* sim, double* rho);
 
@@ -372,6 +383,13 @@ typedef struct {
                              (or as set by rdc_set_step_index) */
     int64_t launches;     /* step-kernel launches enqueued so far */
     void* stream;         /* the simulation's cudaStream_t */
+    int32_t unstable;     /* 1 when forward Euler is linearly unstable at the
+                             rest state of the map's largest phi (the result
+                             rdc_stability returns as RDC_EUNSTABLE_WARN), or
+                             when a caller-owned map has no rest state */
+    int32_t reserved;
+    double stability_rho; /* max |1 + dt lambda| of rdc_stability (NaN when
+                             the map has no rest state) */
 } rdc_view;
 
 /* Fills *out (see rdc_view).  RDC_EINVAL if sim or out is NULL. */
@@ -563,6 +581,12 @@ int rdc_batch_get_info(rdc_batch* b, rdc_batch_info* out);
  * rdc_batch_set_state and rdc_batch_read take).  RDC_EINVAL if b or out is
  * NULL or idx is not a live grid. */
 int rdc_batch_get_grid(rdc_batch* b, int32_t idx, rdc_grid* out);
+
+/* Stability of forward Euler at the rest state of grid idx's largest phi,
+ * as rdc_stability (recorded when the grid was added): *rho receives max
+ * |1 + dt lambda|; returns RDC_EUNSTABLE_WARN when rho > 1, else RDC_OK;
+ * RDC_EINVAL if b or rho is NULL or idx is not a live grid. */
+int rdc_batch_stability(rdc_batch* b, int32_t idx, double* rho);
 
 /*
  * Autotuner: times reps launches of each candidate (single step with 8, 16 or

@@ -66,7 +66,9 @@ class rdc_view(ctypes.Structure):
                 ("phi_pitch_bytes", ctypes.c_size_t), ("width", ctypes.c_int32),
                 ("height", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("elem_bytes", ctypes.c_int32), ("steps_done", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+                ("launches", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("unstable", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stability_rho", ctypes.c_double)]
 
 
 class rdc_launch_shape(ctypes.Structure):
@@ -157,6 +159,7 @@ _SIGS = {
                                             ctypes.c_int32]),
     "rdc_batch_get_info": (ctypes.c_int, [_P, ctypes.POINTER(rdc_batch_info)]),
     "rdc_batch_get_grid": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_grid)]),
+    "rdc_batch_stability": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "rdc_batch_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_batch_info)]),
     "rdc_tune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(rdc_launch_shape),
                                 ctypes.POINTER(ctypes.c_double)]),
@@ -635,6 +638,14 @@ def rdc_batch_get_grid(b, idx: int):
     g = rdc_grid()
     _chk(lib().rdc_batch_get_grid(b, int(idx), ctypes.byref(g)), "rdc_batch_get_grid")
     return g.width, g.height
+
+
+def rdc_batch_stability(b, idx: int):
+    """(status, rho) of grid idx: status RDC_OK or RDC_EUNSTABLE_WARN."""
+    rho = ctypes.c_double()
+    rc = _chk(lib().rdc_batch_stability(b, int(idx), ctypes.byref(rho)), "rdc_batch_stability",
+              allow=(RDC_EUNSTABLE_WARN,))
+    return rc, rho.value
 
 
 def rdc_batch_set_state(b, idx: int, u=None, v=None) -> int:

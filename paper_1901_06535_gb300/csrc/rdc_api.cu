@@ -9,6 +9,7 @@
 // each row starts on a 128-byte boundary and 16-byte vector accesses of any
 // storage type stay aligned.  Plane offsets are multiples of 256 bytes.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -17,9 +18,29 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rdc.h"
 #include "rdc_host.h"
 #include "rdc_internal.h"
+
+static nvtxDomainHandle_t nvtx_domain()
+{
+    static nvtxDomainHandle_t d = nvtxDomainCreateA("librdc");
+    return d;
+}
+
+NvtxRange::NvtxRange(const char* name)
+{
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    nvtxDomainRangePushEx(nvtx_domain(), &a);
+}
+
+NvtxRange::~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
 
 namespace rdc {
 cudaError_t launch_step1_f32(int, const Planes&, const ModelD&, Shape1, cudaStream_t);
@@ -174,7 +195,9 @@ struct rdc_sim {
     float* timelapse = nullptr;   // running maximum of u (lazily allocated)
     bool timelapse_set = false;
     int64_t steps_done = 0, launches = 0;
-    double phi_max = 0.0;
+    double phi_max = 0.0;   // largest phi of the map (an upper bound after drawing)
+    double rho = 0.0;       // stability of forward Euler at the rest state of phi_max
+    bool unstable = false;  // rho > 1
     Shape1 shape1{128, 16};
     ShapeK shapek{64, 32, 1, 256};
 };
@@ -378,11 +401,21 @@ bool host_scan_phi(const void* phi_host, int dtype, int64_t n, const rdc_params*
     return true;
 }
 
+// Records rho and the unstable flag of the current phi_max.
+static void update_stability(rdc_sim* s)
+{
+    double rho = std::nan("");
+    const int rc = host_stability(s->p, s->phi_max, &rho);
+    s->rho = rho;
+    s->unstable = rc != RDC_OK;  // unstable, or (caller-owned map) no rest state at all
+}
+
 static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
                          int phi_dtype, void* stream, void* const* ext_u,
                          void* const* ext_v, const void* ext_phi,
                          size_t ext_pitch_bytes, rdc_sim** out)
 {
+    NvtxRange nvtx("rdc_create");
     if (!out) return RDC_EINVAL;
     *out = nullptr;
     if (g.width < 1 || g.height < 1 || !host_params_valid(p)) return RDC_EINVAL;
@@ -439,6 +472,22 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
             return host_cuda_fail(e, "cudaMalloc(scratch)");
         }
         s->owns_misc = true;
+        // The caller's phi map is not read on the host: its largest value
+        // (for the stability check) comes from the device.
+        long long mx = LLONG_MIN;
+        long long* dmx = reinterpret_cast<long long*>(s->misc);
+        e = cudaMemcpyAsync(dmx, &mx, sizeof mx, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = launch_phi_max(prec, s->phi, s->W, s->H, s->pitch, dmx, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&mx, dmx, sizeof mx, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) {
+            destroy_impl(s);
+            return host_cuda_fail(e, "phi maximum");
+        }
+        const long long bits = mx >= 0 ? mx : (mx ^ 0x7FFFFFFFFFFFFFFFLL);
+        std::memcpy(&s->phi_max, &bits, sizeof bits);
     } else {
         s->pitch = round_up(g.width, 64);
         const size_t sp = (size_t)round_up((int64_t)s->pitch * s->H * esz, 256);
@@ -483,8 +532,33 @@ static int create_common(rdc_grid g, const rdc_params* p, const void* phi_host,
         }
     }
     default_shapes(s);
+    update_stability(s);
     *out = s;
     return RDC_OK;
+}
+
+int host_stability(const rdc_params& p, double phi_max, double* rho_out)
+{
+    double us = 0.0;
+    if (rdc_rest_state(phi_max, p.f, p.q, &us) != RDC_OK) return RDC_EINVAL;
+    // Jacobian of Eq. 1's reaction part at u = v = u*:
+    //   dR/du = 1 - 2u - (f v + phi) 2q/(u+q)^2,  dR/dv = -f (u-q)/(u+q)
+    const double a = 1.0 - 2.0 * us - (p.f * us + phi_max) * 2.0 * p.q / ((us + p.q) * (us + p.q));
+    const double b = -p.f * (us - p.q) / (us + p.q);
+    const double lap_min = -8.0 * p.Du / (p.dx * p.dx);
+    double rho = 0.0;
+    for (int k = 0; k <= 64; ++k) {
+        const double shift = lap_min * k / 64.0;
+        // J = [[a/eps + shift, b/eps], [1, -1]]
+        const double j11 = a / p.eps + shift, j12 = b / p.eps, j21 = 1.0, j22 = -1.0;
+        const double tr = j11 + j22, det = j11 * j22 - j12 * j21;
+        const std::complex<double> disc = std::sqrt(std::complex<double>(tr * tr - 4.0 * det, 0.0));
+        const std::complex<double> l1 = 0.5 * (tr + disc), l2 = 0.5 * (tr - disc);
+        rho = std::max(rho, std::abs(1.0 + p.dt * l1));
+        rho = std::max(rho, std::abs(1.0 + p.dt * l2));
+    }
+    *rho_out = rho;
+    return rho > 1.0 ? RDC_EUNSTABLE_WARN : RDC_OK;
 }
 
 extern "C" {
@@ -554,6 +628,7 @@ int rdc_set_phi(rdc_sim* s, const void* phi_host, int32_t dtype)
     int rc = upload_phi(s, phi_host, dtype);
     if (rc) return rc;
     s->phi_max = mx;
+    update_stability(s);
     return rdc_reset_rest(s);
 }
 
@@ -594,6 +669,7 @@ int rdc_set_state(rdc_sim* s, const void* u_host, const void* v_host, int32_t dt
 
 int rdc_step(rdc_sim* s, int64_t n)
 {
+    NvtxRange nvtx("rdc_step");
     if (!s || n < 0) return RDC_EINVAL;
     ModelD m = model_of(s->p);
     int64_t left = n;
@@ -638,6 +714,7 @@ int rdc_check(rdc_sim* s, int64_t* first_bad)
 
 int rdc_read(rdc_sim* s, void* u_out, void* v_out, int32_t dtype)
 {
+    NvtxRange nvtx("rdc_read");
     if (!s || dtype < 0 || dtype > 3) return RDC_EINVAL;
     const int esz = state_bytes(s->prec);
     const void* src[2] = {s->u[s->cur], s->v[s->cur]};
@@ -716,6 +793,7 @@ int rdc_draw_line(rdc_sim* s, double x0, double y0, double x1, double y1, double
                         s->stream),
        "draw kernel");
     if (value > s->phi_max) s->phi_max = value;
+    update_stability(s);
     return RDC_OK;
 }
 
@@ -748,6 +826,7 @@ int rdc_fill_phi(rdc_sim* s, double value)
     if (!s || !host_phi_ok(value, &s->p)) return RDC_EINVAL;
     CK(launch_fill_phi(s->prec, s->phi, s->W, s->H, s->pitch, value, s->stream), "fill kernel");
     s->phi_max = value;
+    update_stability(s);
     return RDC_OK;
 }
 
@@ -827,27 +906,7 @@ int rdc_rest_state(double phi, double f, double q, double* u_star)
 int rdc_stability(rdc_sim* s, double* rho_out)
 {
     if (!s || !rho_out) return RDC_EINVAL;
-    const rdc_params& p = s->p;
-    double us = 0.0;
-    if (rdc_rest_state(s->phi_max, p.f, p.q, &us) != RDC_OK) return RDC_EINVAL;
-    // Jacobian of Eq. 1's reaction part at u = v = u*:
-    //   dR/du = 1 - 2u - (f v + phi) 2q/(u+q)^2,  dR/dv = -f (u-q)/(u+q)
-    const double a = 1.0 - 2.0 * us - (p.f * us + s->phi_max) * 2.0 * p.q / ((us + p.q) * (us + p.q));
-    const double b = -p.f * (us - p.q) / (us + p.q);
-    const double lap_min = -8.0 * p.Du / (p.dx * p.dx);
-    double rho = 0.0;
-    for (int k = 0; k <= 64; ++k) {
-        const double shift = lap_min * k / 64.0;
-        // J = [[a/eps + shift, b/eps], [1, -1]]
-        const double j11 = a / p.eps + shift, j12 = b / p.eps, j21 = 1.0, j22 = -1.0;
-        const double tr = j11 + j22, det = j11 * j22 - j12 * j21;
-        const std::complex<double> disc = std::sqrt(std::complex<double>(tr * tr - 4.0 * det, 0.0));
-        const std::complex<double> l1 = 0.5 * (tr + disc), l2 = 0.5 * (tr - disc);
-        rho = std::max(rho, std::abs(1.0 + p.dt * l1));
-        rho = std::max(rho, std::abs(1.0 + p.dt * l2));
-    }
-    *rho_out = rho;
-    return rho > 1.0 ? RDC_EUNSTABLE_WARN : RDC_OK;
+    return host_stability(s->p, s->phi_max, rho_out);
 }
 
 int rdc_get_view(rdc_sim* s, rdc_view* out)
@@ -865,6 +924,9 @@ int rdc_get_view(rdc_sim* s, rdc_view* out)
     out->steps_done = s->steps_done;
     out->launches = s->launches;
     out->stream = (void*)s->stream;
+    out->unstable = s->unstable ? 1 : 0;
+    out->reserved = 0;
+    out->stability_rho = s->rho;
     return RDC_OK;
 }
 
@@ -901,6 +963,7 @@ int rdc_set_shape(rdc_sim* s, const rdc_launch_shape* in)
 
 int rdc_tune(rdc_sim* s, int32_t reps, rdc_launch_shape* out, double* best_gcups)
 {
+    NvtxRange nvtx("rdc_tune");
     if (!s || reps < 1) return RDC_EINVAL;
     const ModelD m = model_of(s->p);
     const Planes g{s->u[s->cur], s->v[s->cur], s->phi, s->u[1 - s->cur], s->v[1 - s->cur],

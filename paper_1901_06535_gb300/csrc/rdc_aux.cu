@@ -1,6 +1,7 @@
 // Auxiliary kernels of librdc: rest-state initialisation, catalytic
 // stimulation (§2), the health flag, dtype conversion between packed host
 // order and the pitched device planes, and probe gathers.
+#include <climits>
 #include <cmath>
 
 #include "rdc_device.cuh"
@@ -134,6 +135,29 @@ __global__ void k_health(const S* __restrict__ u, int W, int H, int64_t pitch,
         if (bad_cell(widen(u[i * pitch + j]), q))
             atomicMin(first_bad, (unsigned long long)k);
     }
+}
+
+// Largest phi of a pitched map, as the bit pattern of a double: for IEEE
+// doubles of equal sign the bit patterns, read as signed 64-bit integers,
+// order like the values, and every negative value orders below every positive
+// one, so an atomic maximum over the patterns is the maximum value (a NaN with
+// the sign bit clear orders above +infinity and is reported as such).
+template <typename P>
+__global__ void k_phi_max(const P* __restrict__ phi, int W, int H, int64_t pitch,
+                          long long* out)
+{
+    const int64_t n = (int64_t)W * H;
+    long long m = LLONG_MIN;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / W, j = k - i * W;
+        const double x = (double)phi[i * pitch + j];
+        const long long b = __double_as_longlong(x);
+        // negative values: flip the magnitude bits so that they order too
+        m = max(m, b >= 0 ? b : (long long)(b ^ 0x7FFFFFFFFFFFFFFFLL));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -399,6 +423,18 @@ cudaError_t launch_health(int prec, const void* u, int W, int H, int64_t pitch,
         case P_F16: k_health<__half><<<b, t, 0, st>>>((const __half*)u, W, H, pitch, (float)q, first_bad); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi_max(int prec, const void* phi, int W, int H, int64_t pitch,
+                           long long* out, cudaStream_t st)
+{
+    const int t = 256;
+    const int b = grid_for((int64_t)W * H, t);
+    if (prec == P_F64)
+        k_phi_max<double><<<b, t, 0, st>>>((const double*)phi, W, H, pitch, out);
+    else
+        k_phi_max<float><<<b, t, 0, st>>>((const float*)phi, W, H, pitch, out);
     return cudaGetLastError();
 }
 

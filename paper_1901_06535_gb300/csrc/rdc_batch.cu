@@ -4,6 +4,15 @@
 // all grids from a queue, CUDA graphs of whole step sequences, and an
 // autotuner for the launch shape.
 //
+// Grids join and leave without stalling the host: their memory, the work
+// lists and the descriptor table come from the batch's own stream-ordered
+// memory pool (cudaMallocFromPoolAsync / cudaFreeAsync on the batch's
+// stream, memory kept in the pool for reuse), and every upload is an
+// asynchronous copy on that stream, so rdc_batch_add, rdc_batch_remove and
+// the work-list rebuild they cause enqueue work behind the frames in flight
+// instead of waiting for them (a serving loop keeps polling other streams
+// meanwhile).
+//
 // Each grid in a batch runs the same cell_update as a single simulation with
 // the same parameters, so a grid's result is bit-identical whether it is
 // stepped alone, in a batch, or in any subset of one.
@@ -31,8 +40,11 @@ struct Config {
 };
 
 struct ItemList {
-    Item* dev = nullptr;
+    Item* dev = nullptr;       // device copy (pool memory), capacity `cap` items
     int n = 0;
+    int cap = 0;
+    bool valid = false;        // false: rebuild before the next launch
+    std::vector<Item> host;    // the list as last uploaded
 };
 
 struct GraphEntry {
@@ -51,6 +63,8 @@ struct rdc_batch {
     std::vector<rdc_params> params;
     std::vector<GridDesc> desc;      // host copy; par kept current
     std::vector<void*> mem;          // per-slot allocation (nullptr = free slot)
+    cudaMemPool_t pool = nullptr;    // stream-ordered pool of every device buffer below
+    std::vector<double> phi_max;     // per slot: largest phi of the grid's map
     GridDesc* d_desc = nullptr;
     int d_desc_cap = 0;
     unsigned long long* d_flag = nullptr;  // health flag at +0, work queue at +64
@@ -72,11 +86,29 @@ struct rdc_batch {
 
 namespace {
 
-void free_items(ItemList& L)
+// Stream-ordered allocation from the batch's pool: usable by work enqueued on
+// the batch's stream after this call; no synchronisation.
+cudaError_t dev_alloc(rdc_batch* b, void** p, size_t bytes)
 {
-    if (L.dev) cudaFree(L.dev);
+    return cudaMallocFromPoolAsync(p, bytes, b->pool, b->stream);
+}
+
+// Stream-ordered free: the memory returns to the pool once the work enqueued
+// on the batch's stream before it has finished.
+void dev_free(rdc_batch* b, void* p)
+{
+    if (p) cudaFreeAsync(p, b->stream);
+}
+
+// Marks a work list for rebuilding (its device buffer is kept and reused).
+void invalidate_items(ItemList& L) { L.valid = false; }
+
+void release_items(rdc_batch* b, ItemList& L)
+{
+    dev_free(b, L.dev);
     L.dev = nullptr;
-    L.n = 0;
+    L.n = L.cap = 0;
+    L.valid = false;
 }
 
 void free_graphs(rdc_batch* b)
@@ -102,12 +134,16 @@ int persistent_ctas(int nitems)
 // The two counters of the batched kernels' work queue (zero between launches).
 unsigned* queue_of(rdc_batch* b) { return reinterpret_cast<unsigned*>(b->d_flag) + 16; }
 
+// Rebuilds a work list over every live grid and enqueues its upload on the
+// batch's stream (behind the launches that still read the previous list).
+// The device buffer grows by doubling; nothing waits for the device.
 int build_items(rdc_batch* b, bool stream, ItemList* out)
 {
-    std::vector<Item> items;
     const int cols = stream ? batch_stream_outc(b->prec, b->cfg.k) : batch_step1_cols(b->prec);
     const int rows = stream ? b->cfg.krows : b->cfg.rows;
     if (cols <= 0 || rows <= 0) return RDC_EINVAL;
+    std::vector<Item>& items = out->host;
+    items.clear();
     for (int g = 0; g < b->n; ++g) {
         if (!b->mem[g]) continue;
         const int W = b->grids[g].width, H = b->grids[g].height;
@@ -116,20 +152,35 @@ int build_items(rdc_batch* b, bool stream, ItemList* out)
                 items.push_back(Item{g, x0, y0, std::min(y0 + rows, H)});
     }
     out->n = (int)items.size();
+    out->valid = true;
     if (items.empty()) return RDC_OK;
-    cudaError_t e = cudaMalloc(&out->dev, items.size() * sizeof(Item));
-    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(items)");
-    e = cudaMemcpyAsync(out->dev, items.data(), items.size() * sizeof(Item),
-                        cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMemcpyAsync(items)");
+    if (out->cap < out->n) {
+        dev_free(b, out->dev);
+        out->dev = nullptr;
+        out->cap = 0;
+        const int cap = std::max(1024, 2 * out->n);
+        cudaError_t e = dev_alloc(b, (void**)&out->dev, (size_t)cap * sizeof(Item));
+        if (e != cudaSuccess) {
+            out->valid = false;
+            return host_cuda_fail(e, "cudaMallocFromPoolAsync(items)");
+        }
+        out->cap = cap;
+    }
+    // A pageable source is staged by the runtime before the call returns, so
+    // the host vector may change afterwards.
+    cudaError_t e = cudaMemcpyAsync(out->dev, items.data(), items.size() * sizeof(Item),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) {
+        out->valid = false;
+        return host_cuda_fail(e, "cudaMemcpyAsync(items)");
+    }
     return RDC_OK;
 }
 
 int get_items(rdc_batch* b, bool stream, ItemList** out)
 {
     ItemList& L = stream ? b->stream_items : b->step1_items;
-    if (!L.dev) {
+    if (!L.valid) {
         int rc = build_items(b, stream, &L);
         if (rc) return rc;
     }
@@ -175,14 +226,12 @@ int upload_desc(rdc_batch* b)
 {
     if (b->n == 0) return RDC_OK;
     if (b->d_desc_cap < b->n) {
-        cudaError_t e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamSynchronize");
-        if (b->d_desc) cudaFree(b->d_desc);
+        dev_free(b, b->d_desc);   // after the launches that still read it
         b->d_desc = nullptr;
         b->d_desc_cap = 0;
         const int cap = std::max(16, 2 * b->n);
-        e = cudaMalloc((void**)&b->d_desc, sizeof(GridDesc) * cap);
-        if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(descriptors)");
+        cudaError_t e = dev_alloc(b, (void**)&b->d_desc, sizeof(GridDesc) * cap);
+        if (e != cudaSuccess) return host_cuda_fail(e, "cudaMallocFromPoolAsync(descriptors)");
         b->d_desc_cap = cap;
         free_graphs(b);  // graphs captured the old table's address
     }
@@ -191,21 +240,22 @@ int upload_desc(rdc_batch* b)
     return e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "cudaMemcpyAsync(descriptors)");
 }
 
+// Staging buffer for type conversions of host data (stream-ordered, so the
+// old buffer is released only after the work that still uses it).
 int ensure_stage(rdc_batch* b, size_t bytes)
 {
     if (b->stage_bytes >= bytes) return RDC_OK;
-    cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamSynchronize");
-    if (b->stage) cudaFree(b->stage);
+    dev_free(b, b->stage);
     b->stage = nullptr;
     b->stage_bytes = 0;
-    e = cudaMalloc(&b->stage, bytes);
-    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(stage)");
+    cudaError_t e = dev_alloc(b, &b->stage, bytes);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMallocFromPoolAsync(stage)");
     b->stage_bytes = bytes;
     return RDC_OK;
 }
 
 // Allocates and initialises one grid in slot g (rest state of its phi map).
+// Everything is enqueued on the batch's stream; nothing waits for the device.
 int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const float* phi_host)
 {
     const int prec = b->prec;
@@ -215,8 +265,8 @@ int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const flo
     const size_t sp = r256((size_t)pitch * grid.height * esz);
     const size_t total = 4 * sp + r256((size_t)pitch * grid.height * psz);
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, total);
-    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMalloc(batch grid)");
+    cudaError_t e = dev_alloc(b, &mem, total);
+    if (e != cudaSuccess) return host_cuda_fail(e, "cudaMallocFromPoolAsync(batch grid)");
     e = cudaMemsetAsync(mem, 0, total, b->stream);
     GridDesc d;
     std::memset(&d, 0, sizeof d);
@@ -239,11 +289,18 @@ int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const flo
     d.seed = (unsigned)p.round_seed;
     d.steps = 0;
     if (e == cudaSuccess) {
-        if (phi_host) {
+        if (phi_host && psz == (int)sizeof(float)) {
+            // float maps go straight into the pitched plane (from pinned host
+            // memory this copy does not involve the host at all)
+            e = cudaMemcpy2DAsync((void*)d.phi, (size_t)pitch * psz, phi_host,
+                                  (size_t)grid.width * sizeof(float),
+                                  (size_t)grid.width * sizeof(float), grid.height,
+                                  cudaMemcpyHostToDevice, b->stream);
+        } else if (phi_host) {
             const size_t bytes = (size_t)grid.width * grid.height * sizeof(float);
             int rc = ensure_stage(b, bytes);
             if (rc) {
-                cudaFree(mem);
+                dev_free(b, mem);
                 return rc;
             }
             e = cudaMemcpyAsync(b->stage, phi_host, bytes, cudaMemcpyHostToDevice, b->stream);
@@ -255,9 +312,8 @@ int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const flo
     }
     if (e == cudaSuccess)
         e = launch_rest(prec, d.u[0], d.v[0], d.phi, d.W, d.H, pitch, p.f, p.q, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
-        cudaFree(mem);
+        dev_free(b, mem);
         return host_cuda_fail(e, "batch grid initialisation");
     }
     b->grids[g] = grid;
@@ -267,13 +323,14 @@ int init_slot(rdc_batch* b, int g, rdc_grid grid, const rdc_params& p, const flo
     return RDC_OK;
 }
 
-bool grid_ok(const rdc_batch* b, rdc_grid grid, const rdc_params* p, const float* phi_host)
+bool grid_ok(const rdc_batch* b, rdc_grid grid, const rdc_params* p, const float* phi_host,
+             double* phi_max)
 {
     if (grid.width < 1 || grid.height < 1 || !host_params_valid(p)) return false;
     if (p->precision != b->prec || p->flags != (b->sr ? RDC_STOCH_ROUND : 0)) return false;
-    double mx = 0.0;
+    *phi_max = kPhiActive;
     if (phi_host)
-        return host_scan_phi(phi_host, 0, (int64_t)grid.width * grid.height, p, &mx);
+        return host_scan_phi(phi_host, 0, (int64_t)grid.width * grid.height, p, phi_max);
     return host_phi_ok(kPhiActive, p);
 }
 
@@ -315,8 +372,9 @@ int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
     b->sr = (params[0].flags & RDC_STOCH_ROUND) ? 1 : 0;
     b->cfg.k = b->k_block == 0 ? 1 : b->k_block;
     for (int g = 0; g < n; ++g) {
+        double mx = 0.0;
         if (params[g].k_block != b->k_block ||
-            !grid_ok(b, grids[g], &params[g], phi_host ? phi_host[g] : nullptr)) {
+            !grid_ok(b, grids[g], &params[g], phi_host ? phi_host[g] : nullptr, &mx)) {
             delete b;
             return RDC_EINVAL;
         }
@@ -331,7 +389,27 @@ int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
         }
         b->owns_stream = true;
     }
-    cudaError_t e = cudaMalloc((void**)&b->d_flag, 256);
+    // the stream-ordered pool that grids, work lists and tables come from;
+    // freed memory stays in it for the next grid instead of going back to
+    // the driver
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&b->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(b->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e != cudaSuccess) {
+        rdc_batch_destroy(b);
+        return host_cuda_fail(e, "cudaMemPoolCreate");
+    }
+    e = cudaMalloc((void**)&b->d_flag, 256);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_flag, 0, 256, b->stream);  // queue zeroed
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -353,9 +431,11 @@ int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
 int rdc_batch_add(rdc_batch* b, rdc_grid grid, const rdc_params* p, const float* phi_host,
                   int32_t* idx)
 {
+    NvtxRange nvtx("rdc_batch_add");
     if (!b || !idx || !p) return RDC_EINVAL;
     *idx = -1;
-    if (p->k_block != b->k_block || !grid_ok(b, grid, p, phi_host)) return RDC_EINVAL;
+    double mx = 0.0;
+    if (p->k_block != b->k_block || !grid_ok(b, grid, p, phi_host, &mx)) return RDC_EINVAL;
     int g = 0;
     while (g < b->n && b->mem[g]) ++g;  // reuse a free slot
     if (g == b->n) {
@@ -363,43 +443,48 @@ int rdc_batch_add(rdc_batch* b, rdc_grid grid, const rdc_params* p, const float*
         b->params.push_back(*p);
         b->desc.push_back(GridDesc{});
         b->mem.push_back(nullptr);
+        b->phi_max.push_back(0.0);
         b->n += 1;
     }
     int rc = init_slot(b, g, grid, *p, phi_host);
     if (rc) return rc;
+    b->phi_max[g] = mx;
     free_graphs(b);
-    free_items(b->step1_items);
-    free_items(b->stream_items);
+    invalidate_items(b->step1_items);
+    invalidate_items(b->stream_items);
     *idx = g;
     return RDC_OK;
 }
 
 int rdc_batch_remove(rdc_batch* b, int32_t idx)
 {
+    NvtxRange nvtx("rdc_batch_remove");
     if (!b || idx < 0 || idx >= b->n || !b->mem[idx]) return RDC_EINVAL;
-    cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamSynchronize");
-    cudaFree(b->mem[idx]);
+    // returned to the pool behind the work already enqueued for it; the slot
+    // can take a new grid at once
+    dev_free(b, b->mem[idx]);
     b->mem[idx] = nullptr;
     std::memset(&b->desc[idx], 0, sizeof(GridDesc));
     free_graphs(b);
-    free_items(b->step1_items);
-    free_items(b->stream_items);
+    invalidate_items(b->step1_items);
+    invalidate_items(b->stream_items);
     return RDC_OK;
 }
 
 void rdc_batch_destroy(rdc_batch* b)
 {
     if (!b) return;
-    if (b->stream) cudaStreamSynchronize(b->stream);
     free_graphs(b);
-    free_items(b->step1_items);
-    free_items(b->stream_items);
-    for (void* m : b->mem)
-        if (m) cudaFree(m);
-    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->pool) {
+        release_items(b, b->step1_items);
+        release_items(b, b->stream_items);
+        for (void* m : b->mem) dev_free(b, m);
+        dev_free(b, b->d_desc);
+        dev_free(b, b->stage);
+    }
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->pool) cudaMemPoolDestroy(b->pool);
     if (b->d_flag) cudaFree(b->d_flag);
-    if (b->stage) cudaFree(b->stage);
     if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -452,6 +537,7 @@ int rdc_batch_set_step_index(rdc_batch* b, int32_t idx, int64_t n)
 
 int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n)
 {
+    NvtxRange nvtx("rdc_batch_step");
     if (!b || n < 0) return RDC_EINVAL;
     std::vector<int> subset;
     if (!subset_of(b, idx, m, &subset)) return RDC_EINVAL;
@@ -487,7 +573,11 @@ int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n)
             if (b->graphs.size() >= 64) free_graphs(b);
             it = b->graphs.emplace(key, ge).first;
         }
-        cudaError_t e = cudaGraphLaunch(it->second.exec, b->stream);
+        cudaError_t e;
+        {
+            NvtxRange replay("rdc_batch_step: graph replay");
+            e = cudaGraphLaunch(it->second.exec, b->stream);
+        }
         if (e != cudaSuccess) return host_cuda_fail(e, "cudaGraphLaunch");
         L = it->second.launches;
         b->graph_launches += 1;
@@ -560,10 +650,9 @@ int rdc_batch_set_config(rdc_batch* b, int32_t k, int32_t rows, int32_t krows, i
 {
     if (!b || k < 1 || k > 8 || rows < 1 || krows < 1 || graphs < 0 || graphs > 1)
         return RDC_EINVAL;
-    cudaStreamSynchronize(b->stream);
     free_graphs(b);
-    if (rows != b->cfg.rows) free_items(b->step1_items);
-    if (krows != b->cfg.krows || k != b->cfg.k) free_items(b->stream_items);
+    if (rows != b->cfg.rows) invalidate_items(b->step1_items);
+    if (krows != b->cfg.krows || k != b->cfg.k) invalidate_items(b->stream_items);
     b->cfg.k = k;
     b->cfg.rows = rows;
     b->cfg.krows = krows;
@@ -602,6 +691,12 @@ int rdc_batch_get_grid(rdc_batch* b, int32_t idx, rdc_grid* out)
     return RDC_OK;
 }
 
+int rdc_batch_stability(rdc_batch* b, int32_t idx, double* rho)
+{
+    if (!b || !rho || idx < 0 || idx >= b->n || !b->mem[idx]) return RDC_EINVAL;
+    return host_stability(b->params[idx], b->phi_max[idx], rho);
+}
+
 int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
 {
     if (!b || reps < 1) return RDC_EINVAL;
@@ -633,8 +728,8 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
         b->cfg.k = c.k;
         b->cfg.rows = c.rows;
         b->cfg.krows = c.krows;
-        free_items(b->step1_items);
-        free_items(b->stream_items);
+        invalidate_items(b->step1_items);
+        invalidate_items(b->stream_items);
         ItemList* L = nullptr;
         rc = get_items(b, c.k > 1, &L);
         if (rc) break;
@@ -666,8 +761,8 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    free_items(b->step1_items);
-    free_items(b->stream_items);
+    invalidate_items(b->step1_items);
+    invalidate_items(b->stream_items);
     free_graphs(b);
     b->cfg = rc ? saved : best;
     if (rc) return rc;

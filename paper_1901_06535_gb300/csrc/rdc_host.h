@@ -17,3 +17,19 @@ bool host_scan_phi(const void* phi_host, int dtype, int64_t n, const rdc_params*
 int host_check_device();
 // Records the CUDA error for rdc_last_error; RDC_ENOMEM or RDC_ECUDA.
 int host_cuda_fail(cudaError_t e, const char* what);
+// Linear stability of forward Euler at the rest state of phi_max (the
+// computation of rdc_stability): *rho = max |1 + dt lambda|; returns
+// RDC_EUNSTABLE_WARN when rho > 1, RDC_OK otherwise, RDC_EINVAL when phi_max
+// has no rest state.
+int host_stability(const rdc_params& p, double phi_max, double* rho);
+
+// One call of the C ABI as a named NVTX range (domain "librdc") in profiler
+// timelines: pushed on construction, popped on destruction.  Host side only;
+// with no tool attached it costs a few nanoseconds.
+class NvtxRange {
+public:
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};

@@ -121,6 +121,11 @@ cudaError_t launch_seed(int prec, void* u, int W, int H, int64_t pitch,
 cudaError_t launch_health(int prec, const void* u, int W, int H, int64_t pitch,
                           double q, unsigned long long* first_bad,
                           cudaStream_t st);
+// *out := max(*out, the bit pattern of the largest phi of the map as a
+// double, ordered as a signed integer; see k_phi_max).  The caller
+// initialises *out to LLONG_MIN.
+cudaError_t launch_phi_max(int prec, const void* phi, int W, int H, int64_t pitch,
+                           long long* out, cudaStream_t st);
 // Packed host-order buffer of dtype `src_dtype` -> pitched plane of storage
 // `prec` (RN-even); and back.
 cudaError_t launch_pack_in(int prec, int src_dtype, const void* src, void* dst,

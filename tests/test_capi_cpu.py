@@ -161,6 +161,14 @@ def test_philox_sample_validates_before_touching_the_device(librdc):
     assert lib.rdc_philox_sample(0, None, None, None) == librdc.RDC_OK
 
 
+def test_stability_calls_validate_before_touching_the_device(librdc):
+    import ctypes
+    L = librdc.lib()
+    rho = ctypes.c_double()
+    assert L.rdc_batch_stability(None, 0, ctypes.byref(rho)) == librdc.RDC_EINVAL
+    assert L.rdc_stability(None, ctypes.byref(rho)) == librdc.RDC_EINVAL
+
+
 def test_params_reject_unknown_fields(librdc):
     with pytest.raises(TypeError):
         librdc.rdc_params_default(reserved=0)
