@@ -11,7 +11,8 @@ The JSON line also reports temporal blocking (k steps per launch) and the
 reduced-storage modes as effective GCUPS on the same grid, the end-to-end
 rate through the C ABI with host buffers (phi in, state out, every step),
 the 512-grid parameter sweep (batched kernels, one CUDA graph), the
-64-session serving workload (p50/p99 frame latency), the colour map's rate,
+64-session serving workload (p50/p99 frame latency) and its loaded variant
+(all 64 sessions live, each asking 60 frames per second), the colour map's rate,
 and the FP64 oracle timed on the host cores as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -254,11 +255,12 @@ def main():
                     help="storage of the timed run (default f32; the others are for profiling)")
     ap.add_argument("--stoch", action="store_true",
                     help="stochastic rounding of the 16-bit storage (profiling)")
-    ap.add_argument("--only", default=None, choices=["batch", "render"],
+    ap.add_argument("--only", default=None, choices=["batch", "render", "serve"],
                     help="profiling: run one extra alone and print its JSON (batch: "
                          "--batch-grids grids of the sweep, --euler-steps steps at the "
                          "fixed shape k=6, rows=16, krows=256, no autotuning; render: "
-                         "the colour map of the --grid state)")
+                         "the colour map of the --grid state; serve: both serving "
+                         "workloads)")
     ap.add_argument("--batch-grids", type=int, default=512,
                     help="grids in the sweep of --only batch")
     args = ap.parse_args()
@@ -347,6 +349,7 @@ def main():
         modes["bf16_stoch_tuned"] = _tuned(pkg, stream, "bf16", flags=4)
         extras = {"temporal_blocking_gcups": tb, "tuned_f32": tuned, "storage_modes_gcups": modes,
                   "batch_sweep": _batch_sweep(pkg, stream), "serving": _serving(pkg),
+                  "serving_loaded": _serving_loaded(pkg),
                   "render": _render(pkg, stream, h)}
     e2e = None if args.no_extras else _e2e(pkg, stream, h, disks, nE, args)
 
@@ -540,6 +543,8 @@ def run_only(args):
     if args.only == "batch":
         out = _batch_sweep(pkg, stream, steps=args.euler_steps, n_grids=args.batch_grids,
                            shape=(6, 16, 256))
+    elif args.only == "serve":
+        out = {"serving": _serving(pkg), "serving_loaded": _serving_loaded(pkg)}
     else:
         h = pkg.rdc_create(W, H, pkg.rdc_params_default(precision=args.precision), None,
                            stream.cuda_stream)
@@ -573,6 +578,33 @@ def _serving(pkg, frames=100, steps_per_frame=50):
     st["sessions"] = len(sessions)
     st["frames_per_session"] = frames
     st["steps_per_frame"] = steps_per_frame
+    return st
+
+
+def _serving_loaded(pkg, fps=60.0, seconds=3.0, steps_per_frame=50, rate=64.0):
+    """Interactive serving with every session live at once: the 64 diode
+    sessions of the serving workload (same sizes, maps and touches), arriving
+    Poisson at 64/s, each client asking for a frame at a fixed `fps` for
+    `seconds` (a frame due while its previous one is still on the GPU waits,
+    and its latency counts from its due time); continuous batching, one batch
+    and stream per size class."""
+    from paper_1901_06535_gb300 import serve
+    frames = int(round(fps * seconds))
+    specs = ri.diode_sessions(seed=5, n=64, frames=frames, rate=rate)
+    sessions = [serve.Session(s.sid, s.size, s.size, phi=s.phi, frames=frames,
+                              touches=s.touches, frame_period=1.0 / fps) for s in specs]
+    srv = serve.Server(precision=0, k_block=6, steps_per_frame=steps_per_frame)
+    try:
+        wall, st = serve.run_workload(sessions, [s.arrival for s in specs], srv)
+    finally:
+        srv.close()
+    st["wall_seconds"] = wall
+    st["gcups"] = st["cells_stepped"] / wall / 1e9
+    st["sessions"] = len(sessions)
+    st["frames_per_session"] = frames
+    st["frames_per_second_per_session"] = fps
+    st["steps_per_frame"] = steps_per_frame
+    st["arrival_rate_per_s"] = rate
     return st
 
 

@@ -60,9 +60,9 @@ cudaError_t launch_stream_f64(const Planes&, const ModelD&, int, int, cudaStream
 cudaError_t launch_stream_bf16(const Planes&, const ModelD&, int, int, cudaStream_t);
 cudaError_t launch_stream_f16(const Planes&, const ModelD&, int, int, cudaStream_t);
 #define RDC_DECL_BATCH(n)                                                                   \
-    cudaError_t launch_batch_step1_##n(const GridDesc*, const Item*, int, unsigned*, int,   \
+    cudaError_t launch_batch_step1_##n(const GridDesc*, const TileMap*, int, unsigned*, int,   \
                                        long long, int, int, cudaStream_t);                  \
-    cudaError_t launch_batch_stream_##n(const GridDesc*, const Item*, int, unsigned*, int,  \
+    cudaError_t launch_batch_stream_##n(const GridDesc*, const TileMap*, int, unsigned*, int,  \
                                         int, long long, int, int, cudaStream_t);            \
     int batch_stream_outc_##n(int);
 RDC_DECL_BATCH(f32)
@@ -71,29 +71,29 @@ RDC_DECL_BATCH(bf16)
 RDC_DECL_BATCH(f16)
 #undef RDC_DECL_BATCH
 
-cudaError_t launch_batch_step1(int prec, const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_step1(int prec, const GridDesc* d, const TileMap* map, int rows,
                                unsigned* q, int j, long long sbase, int sr, int ctas,
                                cudaStream_t st)
 {
     switch (prec) {
-        case P_F32: return launch_batch_step1_f32(d, items, nitems, q, j, sbase, sr, ctas, st);
-        case P_F64: return launch_batch_step1_f64(d, items, nitems, q, j, sbase, sr, ctas, st);
-        case P_BF16: return launch_batch_step1_bf16(d, items, nitems, q, j, sbase, sr, ctas, st);
-        case P_F16: return launch_batch_step1_f16(d, items, nitems, q, j, sbase, sr, ctas, st);
+        case P_F32: return launch_batch_step1_f32(d, map, rows, q, j, sbase, sr, ctas, st);
+        case P_F64: return launch_batch_step1_f64(d, map, rows, q, j, sbase, sr, ctas, st);
+        case P_BF16: return launch_batch_step1_bf16(d, map, rows, q, j, sbase, sr, ctas, st);
+        case P_F16: return launch_batch_step1_f16(d, map, rows, q, j, sbase, sr, ctas, st);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batch_stream(int prec, const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_stream(int prec, const GridDesc* d, const TileMap* map, int rows,
                                 unsigned* q, int k, int j, long long sbase, int sr, int ctas,
                                 cudaStream_t st)
 {
     switch (prec) {
-        case P_F32: return launch_batch_stream_f32(d, items, nitems, q, k, j, sbase, sr, ctas, st);
-        case P_F64: return launch_batch_stream_f64(d, items, nitems, q, k, j, sbase, sr, ctas, st);
+        case P_F32: return launch_batch_stream_f32(d, map, rows, q, k, j, sbase, sr, ctas, st);
+        case P_F64: return launch_batch_stream_f64(d, map, rows, q, k, j, sbase, sr, ctas, st);
         case P_BF16:
-            return launch_batch_stream_bf16(d, items, nitems, q, k, j, sbase, sr, ctas, st);
-        case P_F16: return launch_batch_stream_f16(d, items, nitems, q, k, j, sbase, sr, ctas, st);
+            return launch_batch_stream_bf16(d, map, rows, q, k, j, sbase, sr, ctas, st);
+        case P_F16: return launch_batch_stream_f16(d, map, rows, q, k, j, sbase, sr, ctas, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -17,6 +17,7 @@
 // the same parameters, so a grid's result is bit-identical whether it is
 // stepped alone, in a batch, or in any subset of one.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -39,12 +40,13 @@ struct Config {
     int krows = 64;  // rows per item, streamed k-step kernel
 };
 
-struct ItemList {
-    Item* dev = nullptr;       // device copy (pool memory), capacity `cap` items
-    int n = 0;
+// A tile map on the device (see TileMap) with room for `cap` grids, and the
+// host copy it was uploaded from.
+struct MapBuf {
+    TileMap* dev = nullptr;
     int cap = 0;
-    bool valid = false;        // false: rebuild before the next launch
-    std::vector<Item> host;    // the list as last uploaded
+    std::vector<int> host;
+    int total = 0;          // tiles of the map as last built
 };
 
 struct GraphEntry {
@@ -74,10 +76,10 @@ struct rdc_batch {
     bool owns_stream = false;
     Config cfg;
     bool use_graphs = true;
-    // work lists over every live grid (rebuilt when grids join or leave or
-    // the shape changes) and graphs of launch sequences, keyed by
-    // (n, k, rows, krows); the subset of a call is in the descriptors
-    ItemList step1_items, stream_items;
+    // tile maps of the single-step and the k-step kernel, rebuilt for the
+    // grids of every call at fixed device addresses, and graphs of launch
+    // sequences keyed by (n, k, rows, krows), valid for any subset
+    MapBuf map1, mapk;
     std::map<std::vector<int64_t>, GraphEntry> graphs;
     int64_t launches = 0;
     int64_t graph_launches = 0;
@@ -100,15 +102,11 @@ void dev_free(rdc_batch* b, void* p)
     if (p) cudaFreeAsync(p, b->stream);
 }
 
-// Marks a work list for rebuilding (its device buffer is kept and reused).
-void invalidate_items(ItemList& L) { L.valid = false; }
-
-void release_items(rdc_batch* b, ItemList& L)
+void release_map(rdc_batch* b, MapBuf& M)
 {
-    dev_free(b, L.dev);
-    L.dev = nullptr;
-    L.n = L.cap = 0;
-    L.valid = false;
+    dev_free(b, M.dev);
+    M.dev = nullptr;
+    M.cap = 0;
 }
 
 void free_graphs(rdc_batch* b)
@@ -118,101 +116,107 @@ void free_graphs(rdc_batch* b)
     b->graphs.clear();
 }
 
-int persistent_ctas(int nitems)
+int persistent_ctas(int64_t ntiles)
 {
     // 128-thread CTAs, 4 warps each; enough CTAs to fill every SM with as
-    // many as fit (warps take items from a shared queue, so CTAs beyond that
-    // find it empty and end at once), never more than the items need
+    // many as fit (warps take tiles from a shared queue, so CTAs beyond that
+    // find it empty and end at once), never more than the tiles need
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int want = sms * 8;
-    const int need = (nitems + 3) / 4;
-    return std::max(1, std::min(want, need));
+    const int64_t want = sms * 8;
+    const int64_t need = (ntiles + 3) / 4;
+    return (int)std::max<int64_t>(1, std::min(want, need));
 }
 
 // The two counters of the batched kernels' work queue (zero between launches).
 unsigned* queue_of(rdc_batch* b) { return reinterpret_cast<unsigned*>(b->d_flag) + 16; }
 
-// Rebuilds a work list over every live grid and enqueues its upload on the
-// batch's stream (behind the launches that still read the previous list).
-// The device buffer grows by doubling; nothing waits for the device.
-int build_items(rdc_batch* b, bool stream, ItemList* out)
+// Tiles of `cols` x `rows` cells of grid g.
+int64_t grid_tiles(const rdc_batch* b, int g, int cols, int rows, int* tiles_x)
 {
-    const int cols = stream ? batch_stream_outc(b->prec, b->cfg.k) : batch_step1_cols(b->prec);
-    const int rows = stream ? b->cfg.krows : b->cfg.rows;
-    if (cols <= 0 || rows <= 0) return RDC_EINVAL;
-    std::vector<Item>& items = out->host;
-    items.clear();
-    for (int g = 0; g < b->n; ++g) {
-        if (!b->mem[g]) continue;
-        const int W = b->grids[g].width, H = b->grids[g].height;
-        for (int y0 = 0; y0 < H; y0 += rows)
-            for (int x0 = 0; x0 < W; x0 += cols)
-                items.push_back(Item{g, x0, y0, std::min(y0 + rows, H)});
-    }
-    out->n = (int)items.size();
-    out->valid = true;
-    if (items.empty()) return RDC_OK;
-    if (out->cap < out->n) {
-        dev_free(b, out->dev);
-        out->dev = nullptr;
-        out->cap = 0;
-        const int cap = std::max(1024, 2 * out->n);
-        cudaError_t e = dev_alloc(b, (void**)&out->dev, (size_t)cap * sizeof(Item));
-        if (e != cudaSuccess) {
-            out->valid = false;
-            return host_cuda_fail(e, "cudaMallocFromPoolAsync(items)");
-        }
-        out->cap = cap;
-    }
-    // A pageable source is staged by the runtime before the call returns, so
-    // the host vector may change afterwards.
-    cudaError_t e = cudaMemcpyAsync(out->dev, items.data(), items.size() * sizeof(Item),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess) {
-        out->valid = false;
-        return host_cuda_fail(e, "cudaMemcpyAsync(items)");
-    }
-    return RDC_OK;
+    const int W = b->grids[g].width, H = b->grids[g].height;
+    *tiles_x = (W + cols - 1) / cols;
+    return (int64_t)*tiles_x * ((H + rows - 1) / rows);
 }
 
-int get_items(rdc_batch* b, bool stream, ItemList** out)
+// Builds the tile map of `grids` for tiles of `cols` x `rows` cells and
+// enqueues its upload on the batch's stream (behind the launches that still
+// read the previous map; a pageable source is staged before the call
+// returns).  The device buffer keeps its address unless it must grow, which
+// invalidates the captured graphs.
+int build_map(rdc_batch* b, const std::vector<int>& grids, int cols, int rows, MapBuf& M)
 {
-    ItemList& L = stream ? b->stream_items : b->step1_items;
-    if (!L.valid) {
-        int rc = build_items(b, stream, &L);
-        if (rc) return rc;
+    if (cols <= 0 || rows <= 0) return RDC_EINVAL;
+    const int ns = (int)grids.size();
+    std::vector<int>& h = M.host;
+    h.assign(4 + 4 * (size_t)std::max(ns, 1), 0);
+    int64_t total = 0;
+    for (int i = 0; i < ns; ++i) {
+        int tx = 0;
+        const int64_t t = grid_tiles(b, grids[i], cols, rows, &tx);
+        h[4 + 4 * i] = grids[i];
+        h[4 + 4 * i + 1] = tx;
+        h[4 + 4 * i + 2] = (int)total;
+        total += t;
     }
-    *out = &L;
-    return RDC_OK;
+    if (total > INT_MAX) return RDC_EUNSUPPORTED;
+    h[0] = ns;
+    h[1] = (int)total;
+    M.total = (int)total;
+    const int need = std::max(ns, 1);
+    if (M.cap < need) {
+        release_map(b, M);
+        const int cap = std::max(16, 2 * std::max(need, b->n));
+        cudaError_t e = dev_alloc(b, (void**)&M.dev, sizeof(int) * (4 + 4 * (size_t)cap));
+        if (e != cudaSuccess) return host_cuda_fail(e, "cudaMallocFromPoolAsync(tile map)");
+        M.cap = cap;
+        free_graphs(b);  // graphs captured the old map's address
+    }
+    cudaError_t e = cudaMemcpyAsync(M.dev, h.data(), sizeof(int) * h.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    return e == cudaSuccess ? RDC_OK : host_cuda_fail(e, "cudaMemcpyAsync(tile map)");
+}
+
+// Tile maps of both kernels for the grids of a call.
+int build_maps(rdc_batch* b, const std::vector<int>& grids)
+{
+    int rc = build_map(b, grids, batch_step1_cols(b->prec), b->cfg.rows, b->map1);
+    if (rc == RDC_OK && b->cfg.k > 1)
+        rc = build_map(b, grids, batch_stream_outc(b->prec, b->cfg.k), b->cfg.krows, b->mapk);
+    return rc;
+}
+
+// Tiles of every live grid for the current shape (kernel k > 1: streamed).
+int64_t live_tiles(const rdc_batch* b, bool streamed)
+{
+    const int cols = streamed ? batch_stream_outc(b->prec, b->cfg.k) : batch_step1_cols(b->prec);
+    const int rows = streamed ? b->cfg.krows : b->cfg.rows;
+    int64_t t = 0;
+    for (int g = 0; g < b->n; ++g) {
+        int tx = 0;
+        if (b->mem[g]) t += grid_tiles(b, g, cols, rows, &tx);
+    }
+    return t;
 }
 
 // Enqueues the launch sequence of n steps for the subset: n / k streamed
 // k-step launches, then n % k single steps; launch j reads buffer
 // (par + j) & 1 of each grid.
-int enqueue_sequence(rdc_batch* b, int64_t n, int64_t* launches)
+int enqueue_sequence(rdc_batch* b, int64_t n, int ctas1, int ctask, int64_t* launches)
 {
     const int k = b->cfg.k;
-    ItemList* s1 = nullptr;
-    ItemList* sk = nullptr;
-    int rc = get_items(b, false, &s1);
-    if (rc) return rc;
-    if (k > 1) {
-        rc = get_items(b, true, &sk);
-        if (rc) return rc;
-    }
     int64_t j = 0, left = n;
     while (left > 0) {
         cudaError_t e;
         const long long sbase = (long long)(n - left);  // steps of this call already enqueued
         if (k > 1 && left >= k) {
-            e = launch_batch_stream(b->prec, b->d_desc, sk->dev, sk->n, queue_of(b), k,
-                                    (int)(j & 1), sbase, b->sr, persistent_ctas(sk->n), b->stream);
+            e = launch_batch_stream(b->prec, b->d_desc, b->mapk.dev, b->cfg.krows, queue_of(b),
+                                    k, (int)(j & 1), sbase, b->sr, ctask, b->stream);
             left -= k;
         } else {
-            e = launch_batch_step1(b->prec, b->d_desc, s1->dev, s1->n, queue_of(b), (int)(j & 1),
-                                   sbase, b->sr, persistent_ctas(s1->n), b->stream);
+            e = launch_batch_step1(b->prec, b->d_desc, b->map1.dev, b->cfg.rows, queue_of(b),
+                                   (int)(j & 1), sbase, b->sr, ctas1, b->stream);
             left -= 1;
         }
         if (e != cudaSuccess) return host_cuda_fail(e, "batched step kernel");
@@ -449,9 +453,7 @@ int rdc_batch_add(rdc_batch* b, rdc_grid grid, const rdc_params* p, const float*
     int rc = init_slot(b, g, grid, *p, phi_host);
     if (rc) return rc;
     b->phi_max[g] = mx;
-    free_graphs(b);
-    invalidate_items(b->step1_items);
-    invalidate_items(b->stream_items);
+    free_graphs(b);  // their CTA counts were sized for the previous grids
     *idx = g;
     return RDC_OK;
 }
@@ -466,8 +468,6 @@ int rdc_batch_remove(rdc_batch* b, int32_t idx)
     b->mem[idx] = nullptr;
     std::memset(&b->desc[idx], 0, sizeof(GridDesc));
     free_graphs(b);
-    invalidate_items(b->step1_items);
-    invalidate_items(b->stream_items);
     return RDC_OK;
 }
 
@@ -476,8 +476,8 @@ void rdc_batch_destroy(rdc_batch* b)
     if (!b) return;
     free_graphs(b);
     if (b->pool) {
-        release_items(b, b->step1_items);
-        release_items(b, b->stream_items);
+        release_map(b, b->map1);
+        release_map(b, b->mapk);
         for (void* m : b->mem) dev_free(b, m);
         dev_free(b, b->d_desc);
         dev_free(b, b->stage);
@@ -546,19 +546,23 @@ int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n)
     for (int g : subset) b->desc[g].active = 1;
     int rc = upload_desc(b);
     if (rc) return rc;
-    // build the work lists outside any capture (they allocate)
-    ItemList* tmp = nullptr;
-    if ((rc = get_items(b, false, &tmp))) return rc;
-    if (b->cfg.k > 1 && (rc = get_items(b, true, &tmp))) return rc;
+    // the tile maps of this call's grids, outside any capture (they may
+    // allocate); a captured graph reads them at their fixed addresses
+    if ((rc = build_maps(b, subset))) return rc;
     int64_t L = 0;
     if (b->use_graphs) {
+        // a graph serves every subset, so its persistent launches are sized
+        // for all live grids (CTAs beyond the call's tiles find the queue
+        // empty and end at once)
+        const int ctas1 = persistent_ctas(live_tiles(b, false));
+        const int ctask = b->cfg.k > 1 ? persistent_ctas(live_tiles(b, true)) : 1;
         const std::vector<int64_t> key{n, b->cfg.k, b->cfg.rows, b->cfg.krows};
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return host_cuda_fail(e, "cudaStreamBeginCapture");
-            rc = enqueue_sequence(b, n, &L);
+            rc = enqueue_sequence(b, n, ctas1, ctask, &L);
             e = cudaStreamEndCapture(b->stream, &graph);
             if (rc) {
                 if (graph) cudaGraphDestroy(graph);
@@ -582,7 +586,8 @@ int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n)
         L = it->second.launches;
         b->graph_launches += 1;
     } else {
-        rc = enqueue_sequence(b, n, &L);
+        rc = enqueue_sequence(b, n, persistent_ctas(b->map1.total),
+                              b->cfg.k > 1 ? persistent_ctas(b->mapk.total) : 1, &L);
         if (rc) return rc;
     }
     for (int g : subset) {
@@ -651,8 +656,6 @@ int rdc_batch_set_config(rdc_batch* b, int32_t k, int32_t rows, int32_t krows, i
     if (!b || k < 1 || k > 8 || rows < 1 || krows < 1 || graphs < 0 || graphs > 1)
         return RDC_EINVAL;
     free_graphs(b);
-    if (rows != b->cfg.rows) invalidate_items(b->step1_items);
-    if (krows != b->cfg.krows || k != b->cfg.k) invalidate_items(b->stream_items);
     b->cfg.k = k;
     b->cfg.rows = rows;
     b->cfg.krows = krows;
@@ -699,11 +702,16 @@ int rdc_batch_stability(rdc_batch* b, int32_t idx, double* rho)
 
 int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
 {
+    NvtxRange nvtx("rdc_batch_tune");
     if (!b || reps < 1) return RDC_EINVAL;
     double cells = 0;
+    std::vector<int> live;
     for (int g = 0; g < b->n; ++g) {
         b->desc[g].active = b->mem[g] ? 1 : 0;
-        if (b->mem[g]) cells += (double)b->grids[g].width * b->grids[g].height;
+        if (b->mem[g]) {
+            cells += (double)b->grids[g].width * b->grids[g].height;
+            live.push_back(g);
+        }
     }
     if (cells == 0) return RDC_EINVAL;
     int rc = upload_desc(b);
@@ -728,19 +736,17 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
         b->cfg.k = c.k;
         b->cfg.rows = c.rows;
         b->cfg.krows = c.krows;
-        invalidate_items(b->step1_items);
-        invalidate_items(b->stream_items);
-        ItemList* L = nullptr;
-        rc = get_items(b, c.k > 1, &L);
+        rc = build_maps(b, live);
         if (rc) break;
         // Every timed launch reads the current buffers (j = 0) and writes the
         // spare ones, so tuning never advances the state.
         auto launch = [&]() {
-            return c.k > 1 ? launch_batch_stream(b->prec, b->d_desc, L->dev, L->n, queue_of(b),
-                                                 c.k, 0, 0, b->sr, persistent_ctas(L->n),
-                                                 b->stream)
-                           : launch_batch_step1(b->prec, b->d_desc, L->dev, L->n, queue_of(b),
-                                                0, 0, b->sr, persistent_ctas(L->n), b->stream);
+            return c.k > 1 ? launch_batch_stream(b->prec, b->d_desc, b->mapk.dev, c.krows,
+                                                 queue_of(b), c.k, 0, 0, b->sr,
+                                                 persistent_ctas(b->mapk.total), b->stream)
+                           : launch_batch_step1(b->prec, b->d_desc, b->map1.dev, c.rows,
+                                                queue_of(b), 0, 0, b->sr,
+                                                persistent_ctas(b->map1.total), b->stream);
         };
         cudaError_t e = launch();  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
@@ -761,8 +767,6 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    invalidate_items(b->step1_items);
-    invalidate_items(b->stream_items);
     free_graphs(b);
     b->cfg = rc ? saved : best;
     if (rc) return rc;

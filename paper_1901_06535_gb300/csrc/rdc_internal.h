@@ -58,9 +58,10 @@ struct Planes {
 // One grid of a batch, as the batched kernels read it from device memory.
 // par is the index (0/1) of the current buffer when the batch launch
 // sequence starts; launch j of a sequence reads buffer (par + j) & 1 and
-// writes the other.  Grids with active == 0 are skipped by every launch of
-// the sequence, so one work list (and one captured graph) serves any subset.  Model constants stay FP64 here and are rounded to the
-// compute precision per work item, exactly as the single-grid launchers do.
+// writes the other.  The grids a call steps are those of its tile map, so
+// one captured graph serves any subset.  Model constants stay FP64 here and
+// are rounded to the compute precision per work item, exactly as the
+// single-grid launchers do.
 struct GridDesc {
     void* u[2];
     void* v[2];
@@ -69,17 +70,33 @@ struct GridDesc {
     long long pitch;  // elements, all planes
     double eps, f, q, Du, dt, inv_dx2;
     int par;
-    int active;       // 0: this call leaves the grid alone (its items are skipped)
+    int active;       // 1: stepped by the current call (host bookkeeping; the
+                      // kernels take the call's grids from its tile map)
     unsigned seed;    // stochastic rounding key (RDC_STOCH_ROUND)
     int pad_;
     long long steps;  // Euler steps taken by the grid before the current call
 };
 
-// A work item of a batched launch: one warp's strip of one grid.
-//   single step : columns [x0, x0 + 32 * VEC), rows [y0, y1)
-//   streamed k  : output columns [x0, x0 + OUTC), rows [y0, y1)
-struct Item {
-    int g, x0, y0, y1;
+// The work of a batched launch: every grid of the call cut into tiles of
+// `cols` x `rows` cells (the last column and row of tiles partial), one tile
+// per work item of a warp:
+//   single step : cols = 32 * VEC cells (one 16-byte vector per lane)
+//   streamed k  : cols = OUTC output columns
+// The tiles of the call's grids are numbered consecutively, grid after grid,
+// row-major within a grid; span i lists grid g_i, its tiles per row, and the
+// number of the grid's first tile.  The map holds only the grids the call
+// steps, so a launch over a few grids of a large batch touches nothing else.
+struct TileSpan {
+    int g;        // grid (slot) index into the descriptor table
+    int tiles_x;  // tiles per row of that grid
+    int first;    // number of its first tile
+    int pad;
+};
+struct TileMap {
+    int nspans;   // grids in the call
+    int total;    // tiles in the call (the work items)
+    int pad[2];
+    TileSpan span[1];  // nspans entries (the map is allocated for its capacity)
 };
 
 // Kernels of rdc_step_*.cu.
@@ -90,16 +107,16 @@ cudaError_t launch_stepk(int prec, int mode, const Planes& g, const ModelD& m,
 size_t stepk_smem_bytes(int prec, ShapeK s);
 cudaError_t launch_stream(int prec, const Planes& g, const ModelD& m, int k, int rows,
                           cudaStream_t st);
-// Batched launches over a device item list (persistent: `ctas` CTAs of 128
-// threads; each warp takes the next item from the work queue `queue`, two
-// zeroed counters that the launch leaves zeroed); launch index j selects
-// buffers.  sbase: Euler steps of the call before this launch (the rounding
+// Batched launches over the tiles of a device tile map, `rows` rows per tile
+// (persistent: `ctas` CTAs of 128 threads; each warp takes the next tile from
+// the work queue `queue`, two zeroed counters that the launch leaves zeroed);
+// launch index j selects buffers.  sbase: Euler steps of the call before this launch (the rounding
 // stream's step index is the grid's steps + sbase + level); sr: stochastic
 // rounding.
-cudaError_t launch_batch_step1(int prec, const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_step1(int prec, const GridDesc* d, const TileMap* map, int rows,
                                unsigned* queue, int j, long long sbase, int sr, int ctas,
                                cudaStream_t st);
-cudaError_t launch_batch_stream(int prec, const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_stream(int prec, const GridDesc* d, const TileMap* map, int rows,
                                 unsigned* queue, int k, int j, long long sbase, int sr,
                                 int ctas, cudaStream_t st);
 // Columns a warp covers (single step) / writes (streamed, k steps).

@@ -21,16 +21,16 @@ cudaError_t launch_stream_f32(const Planes& g, const ModelD& m, int k, int rows,
     return launch_stream_t<float>(g, m, k, rows, st);
 }
 
-cudaError_t launch_batch_step1_f32(const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_step1_f32(const GridDesc* d, const TileMap* map, int rows,
     unsigned* queue, int j, long long sbase, int sr, int ctas, cudaStream_t st)
 {
-    return launch_batch_step1_t<float>(d, items, nitems, queue, j, sbase, sr, ctas, st);
+    return launch_batch_step1_t<float>(d, map, rows, queue, j, sbase, sr, ctas, st);
 }
 
-cudaError_t launch_batch_stream_f32(const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_stream_f32(const GridDesc* d, const TileMap* map, int rows,
     unsigned* queue, int k, int j, long long sbase, int sr, int ctas, cudaStream_t st)
 {
-    return launch_batch_stream_t<float>(d, items, nitems, queue, k, j, sbase, sr, ctas, st);
+    return launch_batch_stream_t<float>(d, map, rows, queue, k, j, sbase, sr, ctas, st);
 }
 
 int batch_stream_outc_f32(int k) { return stream_outc_t<float>(k); }

@@ -205,42 +205,43 @@ __device__ __forceinline__ Model<T> model_of(const GridDesc& d)
     return m;
 }
 
-// Persistent single step over a batch of grids: every warp takes items from
-// the work queue until the list is exhausted; each item is one warp's strip
-// of one grid.
+// Persistent single step over a batch of grids: every warp takes tiles from
+// the work queue until the map is exhausted; a tile is one warp's strip of
+// 32 vectors of one grid.
 template <typename S, int MODE>
 __global__ void __launch_bounds__(128)
-k_step1_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
+k_step1_batch(const GridDesc* __restrict__ descs, const TileMap* __restrict__ map, int rows,
               unsigned* queue, int j, long long sbase)
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
+    constexpr int COLS = 32 * Traits<S>::VEC;
     pdl_enter();
-    for (int it = queue_next(queue); it < nitems; it = queue_next(queue)) {
-        const Item item = items[it];
-        const GridDesc& d = descs[item.g];
-        if (!d.active) continue;
+    const int total = map->total;
+    for (int it = queue_next(queue); it < total; it = queue_next(queue)) {
+        int g, x0, y0;
+        map_tile(map, it, COLS, rows, g, x0, y0);
+        const GridDesc& d = descs[g];
         const int par = (d.par + j) & 1;
         Model<T> m = model_of<T>(d);
         m.step0 += sbase;
         step1_warp<S, MODE>(static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
                             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
-                            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0,
-                            item.y0, item.y1, m);
+                            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, x0, y0,
+                            min(y0 + rows, d.H), m);
     }
     queue_done(queue);
 }
 
 template <typename S>
-cudaError_t launch_batch_step1_t(const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_step1_t(const GridDesc* d, const TileMap* map, int rows,
                                  unsigned* queue, int j, long long sbase, int sr, int ctas,
                                  cudaStream_t st)
 {
-    if (nitems <= 0) return cudaSuccess;
-    if (ctas < 1) return cudaErrorInvalidValue;
+    if (ctas < 1 || rows < 1) return cudaErrorInvalidValue;
     return dispatch_full<S>(sr != 0, [&](auto mc) {
         return launch_pdl(k_step1_batch<S, decltype(mc)::value>, dim3(ctas), dim3(128), 0, st, d,
-                          items, nitems, queue, j, sbase);
+                          map, rows, queue, j, sbase);
     });
 }
 

@@ -368,42 +368,44 @@ k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
 // Persistent k-step launch over a batch of grids (see k_step1_batch).
 template <typename S, int MODE, int K, int N>
 __device__ __forceinline__ void stream_batch_body(const GridDesc* __restrict__ descs,
-                                                  const Item* __restrict__ items, int nitems,
+                                                  const TileMap* __restrict__ map, int rows,
                                                   unsigned* queue, int j, long long sbase)
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
+    using G = StreamGeom<S, K, N>;
     pdl_enter();
-    for (int it = queue_next(queue); it < nitems; it = queue_next(queue)) {
-        const Item item = items[it];
-        const GridDesc& d = descs[item.g];
-        if (!d.active) continue;
+    const int total = map->total;
+    for (int it = queue_next(queue); it < total; it = queue_next(queue)) {
+        int g, x0, y0;
+        map_tile(map, it, G::OUTC, rows, g, x0, y0);
+        const GridDesc& d = descs[g];
         const int par = (d.par + j) & 1;
         Model<T> m = model_of<T>(d);
         m.step0 += sbase;
         stream_warp<S, MODE, K, N, false>(
             static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
-            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, item.x0, item.y0, item.y1, m);
+            static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, x0, y0, min(y0 + rows, d.H), m);
     }
     queue_done(queue);
 }
 
 template <typename S, int MODE, int K, int N>
 __global__ void __launch_bounds__(128)
-k_stream_batch(const GridDesc* __restrict__ descs, const Item* __restrict__ items, int nitems,
+k_stream_batch(const GridDesc* __restrict__ descs, const TileMap* __restrict__ map, int rows,
                unsigned* queue, int j, long long sbase)
 {
-    stream_batch_body<S, MODE, K, N>(descs, items, nitems, queue, j, sbase);
+    stream_batch_body<S, MODE, K, N>(descs, map, rows, queue, j, sbase);
 }
 
 // The same kernel with its registers capped so that MINB CTAs fit on an SM.
 template <typename S, int MODE, int K, int N, int MINB>
 __global__ void __launch_bounds__(128, MINB)
-k_stream_batch_capped(const GridDesc* __restrict__ descs, const Item* __restrict__ items,
-                      int nitems, unsigned* queue, int j, long long sbase)
+k_stream_batch_capped(const GridDesc* __restrict__ descs, const TileMap* __restrict__ map,
+                      int rows, unsigned* queue, int j, long long sbase)
 {
-    stream_batch_body<S, MODE, K, N>(descs, items, nitems, queue, j, sbase);
+    stream_batch_body<S, MODE, K, N>(descs, map, rows, queue, j, sbase);
 }
 
 // CTAs per SM that the batched kernel is compiled for, 0 = the compiler's
@@ -448,7 +450,7 @@ cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>&
 }
 
 template <typename S, int K>
-cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_stream_batch_k(const GridDesc* d, const TileMap* map, int rows,
                                   unsigned* queue, int j, long long sbase, bool sr, int ctas,
                                   cudaStream_t st)
 {
@@ -457,29 +459,28 @@ cudaError_t launch_stream_batch_k(const GridDesc* d, const Item* items, int nite
         constexpr int MINB = batch_stream_min_ctas<S, K>();
         if constexpr (MINB > 0)
             return launch_pdl(k_stream_batch_capped<S, decltype(mc)::value, K, N, MINB>,
-                              dim3(ctas), dim3(128), 0, st, d, items, nitems, queue, j, sbase);
+                              dim3(ctas), dim3(128), 0, st, d, map, rows, queue, j, sbase);
         else
             return launch_pdl(k_stream_batch<S, decltype(mc)::value, K, N>, dim3(ctas),
-                              dim3(128), 0, st, d, items, nitems, queue, j, sbase);
+                              dim3(128), 0, st, d, map, rows, queue, j, sbase);
     });
 }
 
 template <typename S>
-cudaError_t launch_batch_stream_t(const GridDesc* d, const Item* items, int nitems,
+cudaError_t launch_batch_stream_t(const GridDesc* d, const TileMap* map, int rows,
                                   unsigned* queue, int k, int j, long long sbase, int sr,
                                   int ctas, cudaStream_t st)
 {
-    if (nitems <= 0) return cudaSuccess;
-    if (ctas < 1) return cudaErrorInvalidValue;
+    if (ctas < 1 || rows < 1) return cudaErrorInvalidValue;
     const bool r = sr != 0;
     switch (k) {
-        case 2: return launch_stream_batch_k<S, 2>(d, items, nitems, queue, j, sbase, r, ctas, st);
-        case 3: return launch_stream_batch_k<S, 3>(d, items, nitems, queue, j, sbase, r, ctas, st);
-        case 4: return launch_stream_batch_k<S, 4>(d, items, nitems, queue, j, sbase, r, ctas, st);
-        case 5: return launch_stream_batch_k<S, 5>(d, items, nitems, queue, j, sbase, r, ctas, st);
-        case 6: return launch_stream_batch_k<S, 6>(d, items, nitems, queue, j, sbase, r, ctas, st);
-        case 7: return launch_stream_batch_k<S, 7>(d, items, nitems, queue, j, sbase, r, ctas, st);
-        case 8: return launch_stream_batch_k<S, 8>(d, items, nitems, queue, j, sbase, r, ctas, st);
+        case 2: return launch_stream_batch_k<S, 2>(d, map, rows, queue, j, sbase, r, ctas, st);
+        case 3: return launch_stream_batch_k<S, 3>(d, map, rows, queue, j, sbase, r, ctas, st);
+        case 4: return launch_stream_batch_k<S, 4>(d, map, rows, queue, j, sbase, r, ctas, st);
+        case 5: return launch_stream_batch_k<S, 5>(d, map, rows, queue, j, sbase, r, ctas, st);
+        case 6: return launch_stream_batch_k<S, 6>(d, map, rows, queue, j, sbase, r, ctas, st);
+        case 7: return launch_stream_batch_k<S, 7>(d, map, rows, queue, j, sbase, r, ctas, st);
+        case 8: return launch_stream_batch_k<S, 8>(d, map, rows, queue, j, sbase, r, ctas, st);
     }
     return cudaErrorInvalidValue;
 }

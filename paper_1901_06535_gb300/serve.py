@@ -15,7 +15,16 @@ steps (the paper's "render rate", §2).  The server
     sequence per size class (a session arriving while others are on the GPU
     joins the next tick, so its work overlaps theirs on the device);
   * detects completion with CUDA events and records each frame's latency from
-    request to completion.
+    request to completion.  A client either asks for its next frame as soon as
+    the last one is done, or at a fixed frame rate (``frame_period``); a frame
+    due while the previous one is still on the GPU waits for it, and its
+    latency counts from the moment it was due.
+
+Admission and departure never wait for the device: the library takes a
+session's memory from a stream-ordered pool and enqueues its initialisation
+behind the frames in flight, and the phi maps are copied from page-locked
+host memory (``prepare``), so the loop keeps polling every size class while
+sessions come and go.
 
 All arithmetic runs in librdc; this module only schedules.  A session's
 result is bit-identical to running it alone (tests/test_gpu_serve.py).
@@ -24,6 +33,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import heapq
 import time
 
 import numpy as np
@@ -41,6 +51,8 @@ class Session:
     round_seed: int = 0                     # key of the stochastic rounding (flags RDC_STOCH_ROUND)
     frames: int = 10                        # frames the session will request
     touches: list = dataclasses.field(default_factory=list)  # per frame (cx, cy, r, value) or None
+    frame_period: float = 0.0               # seconds between the client's frame requests
+                                            # (0: the next one as soon as the last is done)
     # filled in by the server
     lane: int = -1
     slot: int = -1
@@ -80,13 +92,17 @@ class Server:
     def __init__(self, precision=C.RDC_F32, k_block: int = 6, steps_per_frame: int = 50,
                  memory_budget: int | None = None, max_sessions: int = 1 << 30,
                  stream=None, graphs: bool = False, flags: int = 0,
-                 lane_cells: tuple = (1 << 19, 1 << 21)):
+                 lane_cells: tuple = (1 << 19, 1 << 21), lane_depth: int = 2):
         """k_block: Euler steps per batched launch (6 measured best for the
         p99 frame latency of the 64-session diode workload with three size
         classes: 1.6-1.7 ms; 8: 1.6-1.8; 4 and 5: 3.1-3.4); flags: 0 or RDC_STOCH_ROUND (16-bit storage), for every
         session.  lane_cells: upper cell counts of the size classes (a last
         class takes the rest); each class has its own batch and stream, or
-        all share `stream` when one is given."""
+        all share `stream` when one is given.  lane_depth: batched frames a
+        size class may have queued on its stream at once (one running, the
+        next waiting); sessions that become ready meanwhile join the
+        following launch, so batches grow with the load instead of the
+        stream filling with many small launches."""
         import torch
         self.torch = torch
         self.precision = precision
@@ -107,7 +123,9 @@ class Server:
         self.waiting: collections.deque[Session] = collections.deque()
         self.active: dict[int, Session] = {}
         self.pending: dict[int, Frame] = {}      # sid -> requested frame not yet launched
-        self.inflight: list = []                 # (event, [frames])
+        self.scheduled: list = []                # heap of (due time, sid, frame index)
+        self.inflight: list = []                 # (event, [frames], lane)
+        self.lane_depth = max(1, int(lane_depth))
         self.completed: list[Frame] = []
         self.ticks = 0
         self.cells_stepped = 0.0
@@ -115,6 +133,19 @@ class Server:
         self.evicted = 0
 
     # -- sessions -------------------------------------------------------------
+    def prepare(self, sessions):
+        """Copies the sessions' phi maps into page-locked host memory (before
+        they arrive), so that admitting a session copies its map to the device
+        asynchronously instead of staging it through the host."""
+        torch = self.torch
+        if not hasattr(torch, "from_numpy"):
+            return
+        for s in sessions:
+            if s.phi is not None and getattr(s, "_pinned", None) is None:
+                t = torch.from_numpy(np.ascontiguousarray(s.phi, dtype=np.float32)).pin_memory()
+                s._pinned = t
+                s.phi = t.numpy()
+
     def arrive(self, s: Session, now: float | None = None):
         s.arrival = time.perf_counter() if now is None else now
         self.waiting.append(s)
@@ -148,8 +179,31 @@ class Server:
         return len(self.lane_cells)
 
     def _request(self, s: Session):
-        if s.done_frames < s.frames:
-            self.pending[s.sid] = Frame(s.sid, s.done_frames, time.perf_counter())
+        """The session's next frame: pending at once, or at its due time when
+        the client asks at a fixed rate (counted from admission)."""
+        if s.done_frames >= s.frames:
+            return
+        now = time.perf_counter()
+        if s.frame_period <= 0.0:
+            self.pending[s.sid] = Frame(s.sid, s.done_frames, now)
+            return
+        due = s.admitted_at + s.done_frames * s.frame_period
+        if due <= now:
+            self.pending[s.sid] = Frame(s.sid, s.done_frames, due)
+        else:
+            heapq.heappush(self.scheduled, (due, s.sid, s.done_frames))
+
+    def _release_due(self):
+        """Moves the frames whose due time has come to the pending set."""
+        now = time.perf_counter()
+        while self.scheduled and self.scheduled[0][0] <= now:
+            due, sid, idx = heapq.heappop(self.scheduled)
+            if sid in self.active:
+                self.pending[sid] = Frame(sid, idx, due)
+
+    def next_due(self) -> float | None:
+        """perf_counter time of the next scheduled frame request, if any."""
+        return self.scheduled[0][0] if self.scheduled else None
 
     def _leave(self, s: Session):
         C.rdc_batch_remove(self.lanes[s.lane].batch, s.slot)
@@ -162,8 +216,13 @@ class Server:
         """Launches one batched frame for every session with a pending
         request and none in flight, one launch sequence per size class.
         Returns the number of sessions stepped."""
-        busy = {f.sid for _, fs in self.inflight for f in fs}
-        ready = [sid for sid in self.pending if sid not in busy]
+        self._release_due()
+        busy = {f.sid for _, fs, _ in self.inflight for f in fs}
+        depth: dict[int, int] = {}
+        for _, _, li in self.inflight:
+            depth[li] = depth.get(li, 0) + 1
+        ready = [sid for sid in self.pending if sid not in busy
+                 and depth.get(self.active[sid].lane, 0) < self.lane_depth]
         if not ready:
             return 0
         by_lane: dict[int, list[int]] = {}
@@ -185,7 +244,7 @@ class Server:
             C.rdc_batch_step(lane.batch, slots, self.steps)
             ev = self.torch.cuda.Event()
             ev.record(lane.stream)
-            self.inflight.append((ev, frames))
+            self.inflight.append((ev, frames, li))
         self.ticks += 1
         return len(ready)
 
@@ -193,7 +252,7 @@ class Server:
         """Completes finished frames; returns how many completed."""
         n = 0
         still = []
-        for ev, frames in self.inflight:
+        for ev, frames, li in self.inflight:
             if ev.query():
                 now = time.perf_counter()
                 for f in frames:
@@ -209,7 +268,7 @@ class Server:
                     else:
                         self._request(s)
             else:
-                still.append((ev, frames))
+                still.append((ev, frames, li))
         self.inflight = still
         return n
 
@@ -219,7 +278,10 @@ class Server:
         sessions are unaffected.  Returns False if the session is unknown."""
         if sid in self.pending:
             del self.pending[sid]
-        for _, frames in self.inflight:
+        if any(x[1] == sid for x in self.scheduled):
+            self.scheduled = [x for x in self.scheduled if x[1] != sid]
+            heapq.heapify(self.scheduled)
+        for _, frames, _ in self.inflight:
             frames[:] = [f for f in frames if f.sid != sid]
         if sid in self.active:
             self._leave(self.active[sid])
@@ -233,7 +295,7 @@ class Server:
         return False
 
     def idle(self) -> bool:
-        return not (self.waiting or self.active or self.inflight)
+        return not (self.waiting or self.active or self.inflight or self.scheduled)
 
     def read(self, s: Session, dtype=np.float64):
         u = np.empty((s.height, s.width), dtype=dtype)
@@ -262,6 +324,7 @@ def run_workload(sessions, arrivals, server: Server, poll_sleep: float = 50e-6,
     """Drives a server through a list of sessions arriving at the given times
     (seconds from start).  Returns (wall seconds, stats)."""
     order = sorted(range(len(sessions)), key=lambda i: arrivals[i])
+    server.prepare(sessions)
     t0 = time.perf_counter()
     nxt = 0
     while True:
@@ -276,6 +339,15 @@ def run_workload(sessions, arrivals, server: Server, poll_sleep: float = 50e-6,
         if now > time_limit:
             raise TimeoutError("serving workload did not finish")
         if not launched:
-            time.sleep(poll_sleep)
+            # nothing to launch: sleep, but no longer than until the next
+            # arrival or frame request when no frame is on the GPU
+            wait = poll_sleep
+            if not server.inflight:
+                nexts = [t0 + arrivals[order[nxt]]] if nxt < len(order) else []
+                if server.next_due() is not None:
+                    nexts.append(server.next_due())
+                if nexts:
+                    wait = max(poll_sleep, min(nexts) - time.perf_counter())
+            time.sleep(min(wait, 1e-3))
     server.torch.cuda.synchronize()
     return time.perf_counter() - t0, server.stats()

@@ -191,3 +191,34 @@ def test_serving_size_classes_equal_alone(gpu):
         u, v = finals[s.sid]
         ua, va = _alone(gpu, s, 18)
         assert np.array_equal(u, ua) and np.array_equal(v, va), s.sid
+
+
+def test_serving_bench_configuration_mix_equals_alone(gpu):
+    """The serving benchmark's configuration: diode sessions of 512², 1024² and
+    2048² (at least one of each), k = 6, 50-step frames with a touch before
+    each, Poisson arrivals, half of the clients asking at 60 frames per second:
+    every session's final state equals its solo run bit for bit."""
+    from paper_1901_06535_gb300 import serve
+    specs = ri.diode_sessions(seed=5, n=9, frames=4, rate=200.0)
+    assert {s.size for s in specs} == {512, 1024, 2048}
+    sessions = [serve.Session(s.sid, s.size, s.size, phi=s.phi, frames=4, touches=s.touches,
+                              frame_period=(1.0 / 60.0 if s.sid % 2 else 0.0))
+                for s in specs]
+    srv = serve.Server(precision=0, k_block=6, steps_per_frame=50)
+    finals = {}
+    orig_leave = srv._leave
+
+    def leave(s):
+        finals[s.sid] = srv.read(s)
+        orig_leave(s)
+
+    srv._leave = leave
+    try:
+        wall, st = serve.run_workload(sessions, [s.arrival for s in specs], srv)
+    finally:
+        srv.close()
+    assert st["frames"] == 4 * len(sessions) and st["peak_sessions"] >= 3
+    for s in sessions:
+        u, v = finals[s.sid]
+        ua, va = _alone(gpu, s, 50)
+        assert np.array_equal(u, ua) and np.array_equal(v, va), (s.sid, s.width)

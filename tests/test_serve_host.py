@@ -192,3 +192,60 @@ def test_run_workload_drives_to_completion(fakes, monkeypatch):
     wall, st = serve.run_workload(sessions, [0.0] * 7, srv, poll_sleep=0.0)
     assert st["frames"] == 21 and srv.idle() and wall >= 0
     assert st["p99_ms"] >= st["p50_ms"] >= 0
+
+
+def test_fixed_frame_rate_requests(fakes):
+    """A client asking at a fixed rate: its next frame becomes pending only at
+    its due time (counted from admission), and a frame's latency counts from
+    that due time, not from when the server launched it."""
+    import time
+    s = _session(0, 256, frames=3)
+    s.frame_period = 0.02
+    srv = serve.Server(steps_per_frame=5)
+    srv.arrive(s)
+    assert srv.tick() == 1                      # frame 0 is due at admission
+    _complete_all()
+    srv.poll()
+    assert srv.tick() == 0 and srv.next_due() == pytest.approx(s.admitted_at + 0.02)
+    assert not srv.idle()                       # a request is scheduled
+    time.sleep(0.025)
+    assert srv.tick() == 1                      # frame 1 is due now
+    assert srv.completed[0].requested == s.admitted_at
+    _complete_all()
+    srv.poll()
+    assert srv.completed[1].requested == pytest.approx(s.admitted_at + 0.02)
+    time.sleep(0.02)
+    srv.tick()
+    _complete_all()
+    srv.poll()
+    assert srv.idle() and len(srv.completed) == 3
+
+
+def test_evict_drops_scheduled_requests(fakes):
+    s = _session(0, 256, frames=5)
+    s.frame_period = 10.0
+    srv = serve.Server()
+    srv.arrive(s)
+    srv.tick()
+    _complete_all()
+    srv.poll()
+    assert srv.next_due() is not None
+    assert srv.evict(0)
+    assert srv.next_due() is None and srv.idle()
+
+
+def test_lane_depth_limits_queued_batches(fakes):
+    """With lane_depth 1 a size class launches its next batch only after the
+    one on its stream completes; the sessions that became ready meanwhile go
+    out together."""
+    s = [_session(i, 256, frames=2) for i in range(3)]
+    srv = serve.Server(steps_per_frame=5, lane_depth=1)
+    srv.arrive(s[0])
+    assert srv.tick() == 1
+    srv.arrive(s[1])
+    srv.arrive(s[2])
+    assert srv.tick() == 0                      # the class's stream is busy
+    _complete_all()
+    srv.poll()
+    assert srv.tick() == 3                      # one batch: s0's second frame, s1, s2
+    assert fakes.steps[-1][1] == tuple(sorted(x.slot for x in s))
