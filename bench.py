@@ -74,6 +74,45 @@ def _traffic(kernel: str, cells: int):
     return rec["bytes_per_cell"] * cells
 
 
+def record_traffic(csv_path: str) -> dict:
+    """The traffic record of the single-step FP32 kernel from an ncu CSV log of
+    `dram__bytes_read.sum`, `dram__bytes_write.sum` and `gpu__time_duration.sum`
+    over launches of k_step1<float> on the default grid, keyed to the SHA-256
+    of the kernel's sources as they are when this runs (right after the
+    capture, on the same tree)."""
+    import csv
+    rows = []
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        if "k_step1<float" in r.get("Kernel Name", ""):
+            rows.append(r)
+    by_id = {}
+    for r in rows:
+        val = float(r["Metric Value"].replace(",", ""))
+        unit = r.get("Metric Unit", "")
+        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit, 1.0)
+        by_id.setdefault(r["ID"], {})[r["Metric Name"]] = val * scale
+    launches = [m for m in by_id.values()
+                if "dram__bytes_read.sum" in m and "dram__bytes_write.sum" in m]
+    if not launches:
+        raise SystemExit(f"no k_step1<float> launches with DRAM counters in {csv_path}")
+    rd = float(np.mean([m["dram__bytes_read.sum"] for m in launches]))
+    wr = float(np.mean([m["dram__bytes_write.sum"] for m in launches]))
+    return {"k_step1<float>": {
+        "bytes_per_cell": (rd + wr) / (W * H),
+        "dram_bytes_read_per_launch": rd, "dram_bytes_write_per_launch": wr,
+        "launches": len(launches), "grid": [W, H],
+        "command": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,"
+                   "gpu__time_duration.sum --clock-control none -k regex:k_step1 -s 5 -c 2 "
+                   "--csv --log-file <csv> python bench.py --steps 1 --warmup 3 "
+                   "--no-cpu-baseline --no-extras --euler-steps 50; "
+                   "python bench.py --record-traffic <csv>",
+        "sources_sha256": kernel_sources_sha256(),
+        "note": "mean over the captured launches (both sweep directions); ncu flushes "
+                "the caches before each launch"}}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -263,7 +302,14 @@ def main():
                          "workloads)")
     ap.add_argument("--batch-grids", type=int, default=512,
                     help="grids in the sweep of --only batch")
+    ap.add_argument("--record-traffic", default=None, metavar="CSV",
+                    help="print the traffic record (profiles/traffic.json) computed from "
+                         "the ncu CSV log of a capture of k_step1<float>, keyed to the "
+                         "current kernel sources, and exit")
     args = ap.parse_args()
+    if args.record_traffic:
+        print(json.dumps(record_traffic(args.record_traffic), indent=1))
+        return 0
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.grid:

@@ -64,7 +64,7 @@ cudaError_t launch_stream_f16(const Planes&, const ModelD&, int, int, cudaStream
                                        long long, int, int, cudaStream_t);                  \
     cudaError_t launch_batch_stream_##n(const GridDesc*, const TileMap*, int, unsigned*, int,  \
                                         int, long long, int, int, cudaStream_t);            \
-    int batch_stream_outc_##n(int);
+    int batch_stream_outc_##n(int, bool);
 RDC_DECL_BATCH(f32)
 RDC_DECL_BATCH(f64)
 RDC_DECL_BATCH(bf16)
@@ -100,13 +100,13 @@ cudaError_t launch_batch_stream(int prec, const GridDesc* d, const TileMap* map,
 
 int batch_step1_cols(int prec) { return 32 * vec_cells(prec); }
 
-int batch_stream_outc(int prec, int k)
+int batch_stream_outc(int prec, int k, bool sr)
 {
     switch (prec) {
-        case P_F32: return batch_stream_outc_f32(k);
-        case P_F64: return batch_stream_outc_f64(k);
-        case P_BF16: return batch_stream_outc_bf16(k);
-        case P_F16: return batch_stream_outc_f16(k);
+        case P_F32: return batch_stream_outc_f32(k, sr);
+        case P_F64: return batch_stream_outc_f64(k, sr);
+        case P_BF16: return batch_stream_outc_bf16(k, sr);
+        case P_F16: return batch_stream_outc_f16(k, sr);
     }
     return 0;
 }

@@ -183,14 +183,14 @@ int build_maps(rdc_batch* b, const std::vector<int>& grids)
 {
     int rc = build_map(b, grids, batch_step1_cols(b->prec), b->cfg.rows, b->map1);
     if (rc == RDC_OK && b->cfg.k > 1)
-        rc = build_map(b, grids, batch_stream_outc(b->prec, b->cfg.k), b->cfg.krows, b->mapk);
+        rc = build_map(b, grids, batch_stream_outc(b->prec, b->cfg.k, b->sr != 0), b->cfg.krows, b->mapk);
     return rc;
 }
 
 // Tiles of every live grid for the current shape (kernel k > 1: streamed).
 int64_t live_tiles(const rdc_batch* b, bool streamed)
 {
-    const int cols = streamed ? batch_stream_outc(b->prec, b->cfg.k) : batch_step1_cols(b->prec);
+    const int cols = streamed ? batch_stream_outc(b->prec, b->cfg.k, b->sr != 0) : batch_step1_cols(b->prec);
     const int rows = streamed ? b->cfg.krows : b->cfg.rows;
     int64_t t = 0;
     for (int g = 0; g < b->n; ++g) {

@@ -121,7 +121,7 @@ cudaError_t launch_batch_stream(int prec, const GridDesc* d, const TileMap* map,
                                 int ctas, cudaStream_t st);
 // Columns a warp covers (single step) / writes (streamed, k steps).
 int batch_step1_cols(int prec);
-int batch_stream_outc(int prec, int k);
+int batch_stream_outc(int prec, int k, bool sr);
 // The kernel that rdc_step uses for one launch of k > 1 steps.
 cudaError_t launch_kblock(int prec, int mode, const Planes& g, const ModelD& m,
                           ShapeK s, cudaStream_t st);

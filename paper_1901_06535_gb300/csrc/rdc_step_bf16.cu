@@ -33,6 +33,6 @@ cudaError_t launch_batch_stream_bf16(const GridDesc* d, const TileMap* map, int 
     return launch_batch_stream_t<__nv_bfloat16>(d, map, rows, queue, k, j, sbase, sr, ctas, st);
 }
 
-int batch_stream_outc_bf16(int k) { return stream_outc_t<__nv_bfloat16>(k); }
+int batch_stream_outc_bf16(int k, bool sr) { return stream_outc_t<__nv_bfloat16>(k, sr); }
 
 }  // namespace rdc

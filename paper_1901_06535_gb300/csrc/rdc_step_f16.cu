@@ -33,6 +33,6 @@ cudaError_t launch_batch_stream_f16(const GridDesc* d, const TileMap* map, int r
     return launch_batch_stream_t<__half>(d, map, rows, queue, k, j, sbase, sr, ctas, st);
 }
 
-int batch_stream_outc_f16(int k) { return stream_outc_t<__half>(k); }
+int batch_stream_outc_f16(int k, bool sr) { return stream_outc_t<__half>(k, sr); }
 
 }  // namespace rdc

@@ -33,6 +33,6 @@ cudaError_t launch_batch_stream_f32(const GridDesc* d, const TileMap* map, int r
     return launch_batch_stream_t<float>(d, map, rows, queue, k, j, sbase, sr, ctas, st);
 }
 
-int batch_stream_outc_f32(int k) { return stream_outc_t<float>(k); }
+int batch_stream_outc_f32(int k, bool sr) { return stream_outc_t<float>(k, sr); }
 
 }  // namespace rdc

@@ -33,6 +33,6 @@ cudaError_t launch_batch_stream_f64(const GridDesc* d, const TileMap* map, int r
     return launch_batch_stream_t<double>(d, map, rows, queue, k, j, sbase, sr, ctas, st);
 }
 
-int batch_stream_outc_f64(int k) { return stream_outc_t<double>(k); }
+int batch_stream_outc_f64(int k, bool sr) { return stream_outc_t<double>(k, sr); }
 
 }  // namespace rdc

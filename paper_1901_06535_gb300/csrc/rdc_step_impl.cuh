@@ -58,11 +58,44 @@ cudaError_t dispatch_mode(int mode, bool sr, F&& f)
     return cudaErrorInvalidValue;
 }
 
+// VEC stored values from p: one 16-byte vector (Vec<S>), or, for a BF16 quad,
+// one 8-byte vector.
+template <typename S, int VEC>
+__device__ __forceinline__ void vload(const S* p, typename Traits<S>::T (&o)[VEC], bool stream)
+{
+    if constexpr (VEC == Traits<S>::VEC) {
+        if (stream) Vec<S>::load_stream(p, o);
+        else Vec<S>::load(p, o);
+    } else {
+        static_assert(sizeof(S) == 2 && VEC == 4, "a quad of 16-bit cells");
+        const uint2 r = stream ? __ldcs(reinterpret_cast<const uint2*>(p))
+                               : __ldg(reinterpret_cast<const uint2*>(p));
+        float2 a, b;
+        if constexpr (std::is_same_v<S, __nv_bfloat16>) {
+            a = bf2_to_f2(r.x);
+            b = bf2_to_f2(r.y);
+        } else {
+            a = h2_to_f2(r.x);
+            b = h2_to_f2(r.y);
+        }
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+    }
+}
+
+// Cells per lane of the single-step kernel: one 16-byte vector, except for
+// BF16 with stochastic rounding, which takes one quad (8 bytes) per lane: its
+// random words and rounding then leave room for more resident warps.
+template <typename S, int MODE>
+constexpr int step1_vec()
+{
+    return ((MODE & MODE_SR) != 0 && sizeof(S) == 2) ? 4 : Traits<S>::VEC;
+}
+
 // One warp's share of a single Euler step: 32 vectors of VEC cells starting
 // at column wcol0, rows [row0, row1).  Warps are independent (no shared
 // memory, no block barrier), so the same body serves one grid per launch
 // (k_step1) and a work list over many grids (k_step1_batch).
-template <typename S, int MODE>
+template <typename S, int MODE, int VEC = Traits<S>::VEC>
 __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __restrict__ v,
                                            const typename Traits<S>::PhiT* __restrict__ phi,
                                            S* __restrict__ u1, S* __restrict__ v1, int W,
@@ -70,7 +103,6 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
                                            int row1, const Model<typename Traits<S>::T>& m)
 {
     using T = typename Traits<S>::T;
-    constexpr int VEC = Traits<S>::VEC;
     const int lane = threadIdx.x & 31;
     const int col0 = wcol0 + lane * VEC;
     const bool act = col0 < W;
@@ -80,16 +112,16 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
     for (int e = 0; e < VEC; ++e) un[e] = uc[e] = us[e] = vv[e] = ph[e] = T(0);
 
     if (act) {
-        Vec<S>::load(u + (int64_t)max(row0 - 1, 0) * pitch + col0, un);
-        Vec<S>::load(u + (int64_t)row0 * pitch + col0, uc);
+        vload<S, VEC>(u + (int64_t)max(row0 - 1, 0) * pitch + col0, un, false);
+        vload<S, VEC>(u + (int64_t)row0 * pitch + col0, uc, false);
     }
     for (int r = row0; r < row1; ++r) {
         const int64_t ro = (int64_t)r * pitch;
         const int64_t rso = (int64_t)min(r + 1, H - 1) * pitch;
         T wl = T(0), er = T(0);
         if (act) {
-            Vec<S>::load(u + rso + col0, us);
-            Vec<S>::load_stream(v + ro + col0, vv);
+            vload<S, VEC>(u + rso + col0, us, false);
+            vload<S, VEC>(v + ro + col0, vv, true);
             load_phi<VEC>(phi + ro + col0, ph);
             if (lane == 0) wl = (col0 > 0) ? widen(u[ro + col0 - 1]) : uc[0];
             if (lane == 31 && col0 + VEC < W) er = widen(u[ro + col0 + VEC]);
@@ -98,7 +130,89 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
         const T esh = __shfl_down_sync(0xffffffffu, uc[0], 1);
         if (lane != 0) wl = wsh;
         if (lane != 31) er = esh;
-        if (act) {
+        if constexpr ((MODE & MODE_SR) != 0) {
+            // 16-bit storage with stochastic rounding, one quad at a time --
+            // its two cell pairs, its random words, its rounding, its packed
+            // words -- so that only one quad's values are live at once.  BF16
+            // takes the add-and-carry form of the rule (sr_bf16; the packed
+            // words take the upper halves of the sums directly) unless the
+            // quad holds a NaN, which the paired sum of its values exposes (an
+            // infinity of each sign also sends the quad to the general form,
+            // which is exact for every value); FP16 the general form.
+            if (act) {
+                unsigned pu[VEC / 2], pv[VEC / 2];
+#pragma unroll
+                for (int e = 0; e < VEC; e += 4) {
+                    float2 a2, b2, c2, d2;   // u', v' of cells e, e+1 and e+2, e+3
+#pragma unroll
+                    for (int h = 0; h < 4; h += 2) {
+                        const int x = e + h;
+                        const float c0 = uc[x], c1 = uc[x + 1];
+                        const float2 w2 = make_float2((x == 0) ? wl : uc[x - 1], c0);
+                        const float2 e2 = make_float2(col0 + x >= W - 1 ? c0 : c1,
+                                                      col0 + x + 1 >= W - 1
+                                                          ? c1
+                                                          : ((x + 2 == VEC) ? er : uc[x + 2]));
+                        cell_update2<MODE>(make_float2(c0, c1), w2, e2,
+                                           make_float2(un[x], un[x + 1]),
+                                           make_float2(us[x], us[x + 1]),
+                                           make_float2(vv[x], vv[x + 1]),
+                                           make_float2(ph[x], ph[x + 1]), m, h ? c2 : a2,
+                                           h ? d2 : b2);
+                    }
+                    const Philox4 rb = sr_quad_bits(m.seed, (col0 + e) >> 2, r, m.step0 + 1);
+                    const float2 chk = __fadd2_rn(__fadd2_rn(a2, b2), __fadd2_rn(c2, d2));
+                    const unsigned w[4] = {rb.x, rb.y, rb.z, rb.w};
+                    auto pack = [](float a, float b) {
+                        if constexpr (std::is_same_v<S, __nv_bfloat16>) return f2_to_bf2(a, b);
+                        else return f2_to_h2(a, b);
+                    };
+                    if (std::is_same_v<S, __nv_bfloat16> && !(isnan(chk.x) || isnan(chk.y))) {
+                        pu[e / 2] = pack_upper(sr_bf16_carry(a2.x, w[0] >> 16),
+                                               sr_bf16_carry(a2.y, w[1] >> 16));
+                        pu[e / 2 + 1] = pack_upper(sr_bf16_carry(c2.x, w[2] >> 16),
+                                                   sr_bf16_carry(c2.y, w[3] >> 16));
+                        pv[e / 2] = pack_upper(sr_bf16_carry(b2.x, w[0] & 0xFFFFu),
+                                               sr_bf16_carry(b2.y, w[1] & 0xFFFFu));
+                        pv[e / 2 + 1] = pack_upper(sr_bf16_carry(d2.x, w[2] & 0xFFFFu),
+                                                   sr_bf16_carry(d2.y, w[3] & 0xFFFFu));
+                    } else {
+                        pu[e / 2] = pack(quantize_sr<S>(a2.x, w[0]), quantize_sr<S>(a2.y, w[1]));
+                        pu[e / 2 + 1] = pack(quantize_sr<S>(c2.x, w[2]), quantize_sr<S>(c2.y, w[3]));
+                        pv[e / 2] = pack(quantize_sr<S>(b2.x, w[0] << 16),
+                                         quantize_sr<S>(b2.y, w[1] << 16));
+                        pv[e / 2 + 1] = pack(quantize_sr<S>(d2.x, w[2] << 16),
+                                             quantize_sr<S>(d2.y, w[3] << 16));
+                    }
+                }
+                if (col0 + VEC <= W) {
+                    if constexpr (VEC == 8) {
+                        st16(u1 + ro + col0, make_uint4(pu[0], pu[1], pu[2], pu[3]));
+                        st16(v1 + ro + col0, make_uint4(pv[0], pv[1], pv[2], pv[3]));
+                    } else {
+                        *reinterpret_cast<uint2*>(u1 + ro + col0) = make_uint2(pu[0], pu[1]);
+                        *reinterpret_cast<uint2*>(v1 + ro + col0) = make_uint2(pv[0], pv[1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        if (col0 + e < W) {
+                            const int sh = 16 * (e & 1);
+                            const unsigned short hu = (unsigned short)(pu[e / 2] >> sh);
+                            const unsigned short hv = (unsigned short)(pv[e / 2] >> sh);
+                            if constexpr (std::is_same_v<S, __nv_bfloat16>) {
+                                u1[ro + col0 + e] = __ushort_as_bfloat16(hu);
+                                v1[ro + col0 + e] = __ushort_as_bfloat16(hv);
+                            } else {
+                                u1[ro + col0 + e] = __ushort_as_half(hu);
+                                v1[ro + col0 + e] = __ushort_as_half(hv);
+                            }
+                        }
+                    }
+                }
+            }
+        } else if (act) {
+            static_assert(VEC == Traits<S>::VEC, "16-byte vectors outside the stochastic rounding path");
             T ou[VEC], ov[VEC];
             if constexpr (sizeof(T) == 4) {
                 // FP32 compute: neighbouring cells in pairs (cell_update2)
@@ -165,18 +279,32 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
     }
 }
 
-// At most 72 registers: the 16-bit-storage instantiations (8 cells per
-// thread) would otherwise take 73 and fit one CTA fewer per SM.  The
-// stochastic-rounding ones need more for the random words (capped at 72
-// they spilled to local memory).
+// Register caps: at most 72 registers, so that the 16-bit-storage
+// instantiations (8 cells per thread) fit 7 CTAs per SM; with stochastic
+// rounding (4 cells per thread) BF16 and FP16 are capped at RDC_SR_BF16_REGS
+// and RDC_SR_F16_REGS.
+#ifndef RDC_SR_BF16_REGS
+#define RDC_SR_BF16_REGS 64
+#endif
+#ifndef RDC_SR_F16_REGS
+#define RDC_SR_F16_REGS 64
+#endif
 template <typename S, int MODE>
-__global__ void __maxnreg__((MODE & MODE_SR) ? 128 : 72)
+constexpr int step1_max_regs()
+{
+    return (MODE & MODE_SR) == 0 ? 72
+                                 : (std::is_same_v<S, __nv_bfloat16> ? RDC_SR_BF16_REGS
+                                                                     : RDC_SR_F16_REGS);
+}
+
+template <typename S, int MODE>
+__global__ void __maxnreg__((step1_max_regs<S, MODE>()))
 k_step1(const S* __restrict__ u, const S* __restrict__ v,
         const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
         S* __restrict__ v1, int W, int H, int64_t pitch, int rows,
         Model<typename Traits<S>::T> m, int flip)
 {
-    constexpr int VEC = Traits<S>::VEC;
+    constexpr int VEC = step1_vec<S, MODE>();
     pdl_enter();
     const int wcol0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * VEC;
     // Consecutive launches sweep the rows in opposite directions (flip), so a
@@ -185,7 +313,8 @@ k_step1(const S* __restrict__ u, const S* __restrict__ v,
     // 16-bit storage.  The order does not change any result (Jacobi update).
     const int by = flip ? (int)(gridDim.y - 1 - blockIdx.y) : (int)blockIdx.y;
     const int row0 = by * rows;
-    step1_warp<S, MODE>(u, v, phi, u1, v1, W, H, pitch, wcol0, row0, min(row0 + rows, H), m);
+    step1_warp<S, MODE, VEC>(u, v, phi, u1, v1, W, H, pitch, wcol0, row0, min(row0 + rows, H),
+                             m);
 }
 
 template <typename T>
@@ -356,13 +485,10 @@ cudaError_t launch_step1_t(int mode, const Planes& g, const ModelD& md, Shape1 s
                            cudaStream_t st)
 {
     using PhiT = typename Traits<S>::PhiT;
-    constexpr int VEC = Traits<S>::VEC;
     if (sh.bx < 32 || sh.bx > 256 || (sh.bx % 32) != 0 || sh.rows < 1)
         return cudaErrorInvalidValue;
-    const int vecs = (g.W + VEC - 1) / VEC;
     int rows = sh.rows;
     if ((g.H + rows - 1) / rows > 65535) rows = (g.H + 65534) / 65535;
-    dim3 grid((vecs + sh.bx - 1) / sh.bx, (g.H + rows - 1) / rows);
     auto m = make_model<S>(md);
     const S* u = static_cast<const S*>(g.u);
     const S* v = static_cast<const S*>(g.v);
@@ -371,6 +497,9 @@ cudaError_t launch_step1_t(int mode, const Planes& g, const ModelD& md, Shape1 s
     S* v1 = static_cast<S*>(g.v1);
     const dim3 block(sh.bx);
     return dispatch_mode<S>(mode, md.sr != 0, [&](auto mc) {
+        constexpr int VEC = step1_vec<S, decltype(mc)::value>();
+        const int vecs = (g.W + VEC - 1) / VEC;
+        const dim3 grid((vecs + sh.bx - 1) / sh.bx, (g.H + rows - 1) / rows);
         return launch_pdl(k_step1<S, decltype(mc)::value>, grid, block, 0, st, u, v, phi, u1, v1,
                           g.W, g.H, g.pitch, rows, m, md.flip);
     });

@@ -27,6 +27,50 @@
 
 namespace rdc {
 
+#ifndef RDC_F32_STREAM_UNROLL_K3
+#define RDC_F32_STREAM_UNROLL_K3 1
+#endif
+#ifndef RDC_F32_STREAM_UNROLL_K4
+#define RDC_F32_STREAM_UNROLL_K4 6
+#endif
+#ifndef RDC_F32_STREAM_UNROLL_K5
+#define RDC_F32_STREAM_UNROLL_K5 3
+#endif
+#ifndef RDC_F32_STREAM_UNROLL_K6
+#define RDC_F32_STREAM_UNROLL_K6 6
+#endif
+#ifndef RDC_F32_STREAM_UNROLL_K7
+#define RDC_F32_STREAM_UNROLL_K7 3
+#endif
+#ifndef RDC_F32_STREAM_UNROLL_K8
+#define RDC_F32_STREAM_UNROLL_K8 3
+#endif
+
+// Unroll factor of the streamed kernel's row loop: the three-row register
+// rotation and the K-deep phi queue become renaming when it is a multiple of
+// both; the single-grid FP32 kernel (GH) takes per-K factors.
+template <int K, bool GH>
+constexpr int stream_unroll()
+{
+    if constexpr (!GH) return K >= 4 ? 3 : 1;
+    else
+        return K == 3 ? RDC_F32_STREAM_UNROLL_K3
+             : K == 4 ? RDC_F32_STREAM_UNROLL_K4
+             : K == 5 ? RDC_F32_STREAM_UNROLL_K5
+             : K == 6 ? RDC_F32_STREAM_UNROLL_K6
+             : K == 7 ? RDC_F32_STREAM_UNROLL_K7
+             : K == 8 ? RDC_F32_STREAM_UNROLL_K8 : 1;
+}
+#ifndef RDC_F32_STREAM_MINB_K4
+#define RDC_F32_STREAM_MINB_K4 6
+#endif
+#ifndef RDC_F32_STREAM_MINB_K5
+#define RDC_F32_STREAM_MINB_K5 5
+#endif
+#ifndef RDC_F32_STREAM_MINB_K6
+#define RDC_F32_STREAM_MINB_K6 0
+#endif
+
 // N consecutive stored values (N * sizeof(S) = 4, 8 or 16 bytes) -> compute
 // type (S may also be a phi type: float or double).
 template <typename S>
@@ -87,9 +131,13 @@ __device__ __forceinline__ int reflect_index(int x, int n)
     return x;
 }
 
-template <typename S, int K, int N>
+// With stochastic rounding the overlap is a multiple of 4, so that every
+// warp's first column starts a quad: with two cells per lane, lanes 2j and
+// 2j + 1 then hold the two halves of one quad and share its random words.
+template <typename S, int K, int N, bool SR = false>
 struct StreamGeom {
-    static constexpr int HALO = (K + N - 1) / N * N;  // overlap per side, columns
+    static constexpr int ALIGN = (SR && N < 4) ? 4 : N;
+    static constexpr int HALO = (K + ALIGN - 1) / ALIGN * ALIGN;  // overlap per side, columns
     static constexpr int WCOLS = 32 * N;              // columns a warp holds
     static constexpr int OUTC = WCOLS - 2 * HALO;     // columns a warp writes
     static_assert(OUTC > 0, "halo wider than the warp");
@@ -121,7 +169,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
-    using G = StreamGeom<S, K, N>;
+    using G = StreamGeom<S, K, N, (MODE & MODE_SR) != 0>;
     // GHOST: cells beyond the borders are loaded as mirror images of the cells
     // inside (rows and columns), so the level loop needs no border selects.
     // Addition is commutative, so a mirrored ghost cell evolves exactly like
@@ -186,7 +234,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     // single-grid FP32 kernel at K = 4 (GH) runs best unrolled six times
     // (835 vs 813 G cell-updates/s; six times lost 17 % with 16-bit storage
     // and 3 % in the batched kernel).
-    constexpr int UNROLL = (GH && K == 4) ? 6 : ((K >= 4) ? 3 : 1);
+    constexpr int UNROLL = stream_unroll<K, GH>();
 #pragma unroll UNROLL
     for (int t = t0; t <= t_end; ++t) {
         T nphi[N];
@@ -225,6 +273,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                 Q1[0][e] = Q0[0][e]; Q0[0][e] = nv[e];
             }
         }
+        unsigned wa = 0u, wb = 0u, wa_next = 0u, wb_next = 0u;  // shared random words
 #pragma unroll
         for (int l = 1; l <= K; ++l) {
             const int r = t - l;
@@ -235,12 +284,38 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
             {
                 const T (&ph)[N] = F[l - 1];
                 const bool top = !GHOST && (r == 0), bottom = !GHOST && (r == H - 1);
-                // stochastic rounding: the random words of the lane's quad (its N
-                // cells lie in one quad: N = 2 starts at an even column, N = 4 at
-                // a multiple of 4)
+                // stochastic rounding: the random words of the lane's cells
+                // (wa, wb for N = 2; the whole quad rb for N = 4, whose lanes
+                // start on multiples of 4).  With N = 2 the two lanes of a quad
+                // share its Philox call in pairs of levels: for levels l, l + 1
+                // the lane holding the quad's first half computes the quad's
+                // words of level l, its partner those of level l + 1, and each
+                // hands the other the two words it needs (a last odd level is
+                // computed by both).
+                const int rrow = r;
                 Philox4 rb{0u, 0u, 0u, 0u};
-                if constexpr ((MODE & MODE_SR) != 0)
-                    rb = sr_quad_bits(m.seed, cl >> 2, r, m.step0 + l);
+                if constexpr ((MODE & MODE_SR) != 0 && N == 2) {
+                    const bool second = (cl & 2) != 0;   // the quad's second half
+                    if ((l & 1) == 1 && l < K) {
+                        const Philox4 P = sr_quad_bits(m.seed, cl >> 2, second ? rrow - 1 : rrow,
+                                                       m.step0 + l + (second ? 1 : 0));
+                        const unsigned g0 = __shfl_xor_sync(0xffffffffu, second ? P.x : P.z, 1);
+                        const unsigned g1 = __shfl_xor_sync(0xffffffffu, second ? P.y : P.w, 1);
+                        wa = second ? g0 : P.x;
+                        wb = second ? g1 : P.y;
+                        wa_next = second ? P.z : g0;
+                        wb_next = second ? P.w : g1;
+                    } else if ((l & 1) == 0) {
+                        wa = wa_next;
+                        wb = wb_next;
+                    } else {
+                        const Philox4 P = sr_quad_bits(m.seed, cl >> 2, rrow, m.step0 + l);
+                        wa = second ? P.z : P.x;
+                        wb = second ? P.w : P.y;
+                    }
+                } else if constexpr ((MODE & MODE_SR) != 0) {
+                    rb = sr_quad_bits(m.seed, cl >> 2, rrow, m.step0 + l);
+                }
                 if constexpr (sizeof(T) == 4 && N % 2 == 0) {
                     // FP32 compute: neighbouring cells in pairs (cell_update2).
                     // The border selects also assemble the west and east pairs.
@@ -263,13 +338,36 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                                            make_float2(Q1[l - 1][e], Q1[l - 1][e + 1]),
                                            make_float2(ph[e], ph[e + 1]), m, un, vn);
                         if constexpr ((MODE & MODE_SR) != 0) {
-                            // stochastic rounding of level l (state step0 + l)
-                            const bool hi = (col & 2) != 0;  // words 2, 3 of the quad
-                            const unsigned w0 = hi ? rb.z : rb.x, w1 = hi ? rb.w : rb.y;
-                            nu[e] = quantize_sr<S>(un.x, w0);
-                            nu[e + 1] = quantize_sr<S>(un.y, w1);
-                            nv[e] = quantize_sr<S>(vn.x, w0 << 16);
-                            nv[e + 1] = quantize_sr<S>(vn.y, w1 << 16);
+                            // stochastic rounding of level l (state step0 + l);
+                            // BF16 by the add-and-carry form (sr_bf16), a NaN
+                            // passed on as it is: it stays a NaN through the
+                            // later levels and is stored as the canonical NaN,
+                            // the bits the general form gives (a branch to the
+                            // general form here would double the registers of
+                            // the unrolled level loop)
+                            unsigned w0, w1;
+                            if constexpr (N == 2) {
+                                w0 = wa;
+                                w1 = wb;
+                            } else {
+                                const bool hi = (col & 2) != 0;  // words 2, 3 of the quad
+                                w0 = hi ? rb.z : rb.x;
+                                w1 = hi ? rb.w : rb.y;
+                            }
+                            if constexpr (std::is_same_v<S, __nv_bfloat16>) {
+                                auto sr = [](float x, unsigned r16) {
+                                    return isnan(x) ? x : sr_bf16(x, r16);
+                                };
+                                nu[e] = sr(un.x, w0 >> 16);
+                                nu[e + 1] = sr(un.y, w1 >> 16);
+                                nv[e] = sr(vn.x, w0 & 0xFFFFu);
+                                nv[e + 1] = sr(vn.y, w1 & 0xFFFFu);
+                            } else {
+                                nu[e] = quantize_sr<S>(un.x, w0);
+                                nu[e + 1] = quantize_sr<S>(un.y, w1);
+                                nv[e] = quantize_sr<S>(vn.x, w0 << 16);
+                                nv[e + 1] = quantize_sr<S>(vn.y, w1 << 16);
+                            }
                         } else if constexpr (sizeof(S) == 2) {
                             const float2 qu = quantize2<S>(un), qv = quantize2<S>(vn);
                             nu[e] = qu.x;
@@ -350,19 +448,51 @@ template <typename S, int K>
 constexpr bool stream_ghost() { return sizeof(S) == 4 && K >= 4; }
 
 template <typename S, int MODE, int K, int N>
-__global__ void __launch_bounds__(128)
-k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
-               const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
-               S* __restrict__ v1, int W, int H, int64_t pitch, int rows, int nwarps_x,
-               Model<typename Traits<S>::T> m)
+__device__ __forceinline__ void stepk_stream_body(const S* __restrict__ u, const S* __restrict__ v,
+                                                  const typename Traits<S>::PhiT* __restrict__ phi,
+                                                  S* __restrict__ u1, S* __restrict__ v1, int W,
+                                                  int H, int64_t pitch, int rows, int nwarps_x,
+                                                  const Model<typename Traits<S>::T>& m)
 {
-    using G = StreamGeom<S, K, N>;
+    using G = StreamGeom<S, K, N, (MODE & MODE_SR) != 0>;
     pdl_enter();
     const int wx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wx >= nwarps_x) return;                       // whole warps only
     const int y0 = blockIdx.y * rows;
     stream_warp<S, MODE, K, N, stream_ghost<S, K>()>(u, v, phi, u1, v1, W, H, pitch, wx * G::OUTC, y0,
                                min(y0 + rows, H), m);
+}
+
+template <typename S, int MODE, int K, int N>
+__global__ void __launch_bounds__(128)
+k_stepk_stream(const S* __restrict__ u, const S* __restrict__ v,
+               const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
+               S* __restrict__ v1, int W, int H, int64_t pitch, int rows, int nwarps_x,
+               Model<typename Traits<S>::T> m)
+{
+    stepk_stream_body<S, MODE, K, N>(u, v, phi, u1, v1, W, H, pitch, rows, nwarps_x, m);
+}
+
+// The same kernel with its registers capped so that MINB CTAs fit on an SM.
+template <typename S, int MODE, int K, int N, int MINB>
+__global__ void __launch_bounds__(128, MINB)
+k_stepk_stream_capped(const S* __restrict__ u, const S* __restrict__ v,
+                      const typename Traits<S>::PhiT* __restrict__ phi, S* __restrict__ u1,
+                      S* __restrict__ v1, int W, int H, int64_t pitch, int rows, int nwarps_x,
+                      Model<typename Traits<S>::T> m)
+{
+    stepk_stream_body<S, MODE, K, N>(u, v, phi, u1, v1, W, H, pitch, rows, nwarps_x, m);
+}
+
+// CTAs per SM the single-grid FP32 kernel is compiled for (0: the compiler's
+// choice).
+template <typename S, int MODE, int K>
+constexpr int stream_single_min_ctas()
+{
+    return (sizeof(S) != 4 || (MODE & MODE_SR) != 0)
+               ? 0
+               : (K == 4 ? RDC_F32_STREAM_MINB_K4
+                         : (K == 5 ? RDC_F32_STREAM_MINB_K5 : (K == 6 ? RDC_F32_STREAM_MINB_K6 : 0)));
 }
 
 // Persistent k-step launch over a batch of grids (see k_step1_batch).
@@ -373,7 +503,7 @@ __device__ __forceinline__ void stream_batch_body(const GridDesc* __restrict__ d
 {
     using T = typename Traits<S>::T;
     using PhiT = typename Traits<S>::PhiT;
-    using G = StreamGeom<S, K, N>;
+    using G = StreamGeom<S, K, N, (MODE & MODE_SR) != 0>;
     pdl_enter();
     const int total = map->total;
     for (int it = queue_next(queue); it < total; it = queue_next(queue)) {
@@ -436,16 +566,24 @@ cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>&
 {
     using PhiT = typename Traits<S>::PhiT;
     constexpr int N = StreamVec<S, K>::N;
-    using G = StreamGeom<S, K, N>;
-    const int nwx = (g.W + G::OUTC - 1) / G::OUTC;
     const int wpb = 4;
     if ((g.H + rows - 1) / rows > 65535) return cudaErrorInvalidValue;
-    dim3 grid((nwx + wpb - 1) / wpb, (g.H + rows - 1) / rows);
     return dispatch_full<S>(sr, [&](auto mc) {
-        return launch_pdl(k_stepk_stream<S, decltype(mc)::value, K, N>, grid, dim3(32 * wpb), 0,
-                          st, static_cast<const S*>(g.u), static_cast<const S*>(g.v),
-                          static_cast<const PhiT*>(g.phi), static_cast<S*>(g.u1),
-                          static_cast<S*>(g.v1), g.W, g.H, g.pitch, rows, nwx, m);
+        using G = StreamGeom<S, K, N, (decltype(mc)::value & MODE_SR) != 0>;
+        const int nwx = (g.W + G::OUTC - 1) / G::OUTC;
+        const dim3 grid((nwx + wpb - 1) / wpb, (g.H + rows - 1) / rows);
+        constexpr int MINB = stream_single_min_ctas<S, decltype(mc)::value, K>();
+        if constexpr (MINB > 0)
+            return launch_pdl(k_stepk_stream_capped<S, decltype(mc)::value, K, N, MINB>, grid,
+                              dim3(32 * wpb), 0, st, static_cast<const S*>(g.u),
+                              static_cast<const S*>(g.v), static_cast<const PhiT*>(g.phi),
+                              static_cast<S*>(g.u1), static_cast<S*>(g.v1), g.W, g.H, g.pitch,
+                              rows, nwx, m);
+        else
+            return launch_pdl(k_stepk_stream<S, decltype(mc)::value, K, N>, grid, dim3(32 * wpb),
+                              0, st, static_cast<const S*>(g.u), static_cast<const S*>(g.v),
+                              static_cast<const PhiT*>(g.phi), static_cast<S*>(g.u1),
+                              static_cast<S*>(g.v1), g.W, g.H, g.pitch, rows, nwx, m);
     });
 }
 
@@ -485,18 +623,19 @@ cudaError_t launch_batch_stream_t(const GridDesc* d, const TileMap* map, int row
     return cudaErrorInvalidValue;
 }
 
-// Output columns per warp of the streamed kernel.
+// Output columns per warp of the streamed kernel (sr: with stochastic
+// rounding, whose overlap is a multiple of 4 columns).
 template <typename S>
-int stream_outc_t(int k)
+int stream_outc_t(int k, bool sr)
 {
     switch (k) {
-        case 2: return StreamGeom<S, 2, StreamVec<S, 2>::N>::OUTC;
-        case 3: return StreamGeom<S, 3, StreamVec<S, 3>::N>::OUTC;
-        case 4: return StreamGeom<S, 4, StreamVec<S, 4>::N>::OUTC;
-        case 5: return StreamGeom<S, 5, StreamVec<S, 5>::N>::OUTC;
-        case 6: return StreamGeom<S, 6, StreamVec<S, 6>::N>::OUTC;
-        case 7: return StreamGeom<S, 7, StreamVec<S, 7>::N>::OUTC;
-        case 8: return StreamGeom<S, 8, StreamVec<S, 8>::N>::OUTC;
+        case 2: return sr ? StreamGeom<S, 2, StreamVec<S, 2>::N, true>::OUTC : StreamGeom<S, 2, StreamVec<S, 2>::N>::OUTC;
+        case 3: return sr ? StreamGeom<S, 3, StreamVec<S, 3>::N, true>::OUTC : StreamGeom<S, 3, StreamVec<S, 3>::N>::OUTC;
+        case 4: return sr ? StreamGeom<S, 4, StreamVec<S, 4>::N, true>::OUTC : StreamGeom<S, 4, StreamVec<S, 4>::N>::OUTC;
+        case 5: return sr ? StreamGeom<S, 5, StreamVec<S, 5>::N, true>::OUTC : StreamGeom<S, 5, StreamVec<S, 5>::N>::OUTC;
+        case 6: return sr ? StreamGeom<S, 6, StreamVec<S, 6>::N, true>::OUTC : StreamGeom<S, 6, StreamVec<S, 6>::N>::OUTC;
+        case 7: return sr ? StreamGeom<S, 7, StreamVec<S, 7>::N, true>::OUTC : StreamGeom<S, 7, StreamVec<S, 7>::N>::OUTC;
+        case 8: return sr ? StreamGeom<S, 8, StreamVec<S, 8>::N, true>::OUTC : StreamGeom<S, 8, StreamVec<S, 8>::N>::OUTC;
     }
     return 0;
 }

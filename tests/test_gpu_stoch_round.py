@@ -76,6 +76,10 @@ def test_rounding_is_the_same_for_every_launch(gpu, prec):
     runs = {
         "k4": dict(k=4),
         "k6 rows 7": dict(k=6, shape=dict(k=6, variant=0, krows=7)),
+        "k5 streamed": dict(k=5, shape=dict(k=5, variant=0, krows=16)),
+        "k7 streamed rows 5": dict(k=7, shape=dict(k=7, variant=0, krows=5)),
+        "k3 streamed": dict(k=3, shape=dict(k=3, variant=0, krows=32)),
+        "k2 streamed": dict(k=2, shape=dict(k=2, variant=0, krows=64)),
         "k3 tile": dict(k=3, shape=dict(k=3, variant=1, tx=16, ty=8, nthreads=64)),
         "k8 tile": dict(k=8, shape=dict(k=8, variant=1, tx=40, ty=24, nthreads=128)),
         "k1 rows 3": dict(k=1, shape=dict(rows=3, bx=64)),
@@ -88,6 +92,30 @@ def test_rounding_is_the_same_for_every_launch(gpu, prec):
     u2, _, _ = gpu_run(gpu, W, H, seeds=s, n=n, prec=prec, flags=SR, round_seed=6, k=1)
     urn, _, _ = gpu_run(gpu, W, H, seeds=s, n=n, prec=prec, flags=0, k=1)
     assert not np.array_equal(u2, ref) and not np.array_equal(urn, ref)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f16"])
+def test_nan_cells_are_stored_alike_by_every_launch(gpu, prec):
+    """A state holding NaN (and an infinity): the single step and the
+    streamed kernels store the same bits (non-finite values round to nearest;
+    the NaN spreads), and the health check reports it."""
+    W, H, n = 96, 40, 12
+    p = gpu.rdc_params_default(precision=PREC[prec], flags=SR, round_seed=9)
+    us = gpu.rdc_rest_state(0.054, 1.4, 0.002)
+    u = np.full((H, W), us, dtype=np.float32)
+    v = u.copy()
+    u[20, 30] = np.nan
+    u[5, 70] = np.inf
+    v[33, 10] = np.nan
+    outs = []
+    for k in (1, 4, 5):
+        u_out, v_out, ex = gpu_run(gpu, W, H, n=n, prec=prec, flags=SR, round_seed=9, k=k,
+                                   state=(u, v), dtype=np.float32)
+        assert ex["status"] == gpu.RDC_ENONFINITE
+        outs.append((u_out.view(np.uint32), v_out.view(np.uint32)))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+    assert np.isnan(outs[0][0].view(np.float32)).sum() > 1
 
 
 @pytest.mark.parametrize("prec", ["bf16", "f16"])
