@@ -14,6 +14,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <thread>
 #include <vector>
@@ -362,42 +363,82 @@ static int upload_phi(rdc_sim* s, const void* phi_host, int dtype)
     return RDC_OK;
 }
 
-// Validates every phi value and finds the largest; large maps are split
-// over host threads (each chunk is scanned in order, so the result does not
-// depend on the split).
+// Smallest and largest value of x[k0, k1) and whether any is a NaN, over
+// eight independent lanes without branches (so the compiler can keep the
+// lanes in vector registers).
+template <typename T>
+static void minmax_range(const T* x, int64_t k0, int64_t k1, double* lo, double* hi, bool* nan)
+{
+    T mn[8], mx[8];
+    unsigned bad = 0;
+    for (int i = 0; i < 8; ++i) {
+        mn[i] = std::numeric_limits<T>::infinity();
+        mx[i] = -std::numeric_limits<T>::infinity();
+    }
+    int64_t k = k0;
+    for (; k + 8 <= k1; k += 8)
+        for (int i = 0; i < 8; ++i) {
+            const T v = x[k + i];
+            mn[i] = v < mn[i] ? v : mn[i];
+            mx[i] = v > mx[i] ? v : mx[i];
+            bad |= (unsigned)(v != v);
+        }
+    for (; k < k1; ++k) {
+        const T v = x[k];
+        mn[0] = v < mn[0] ? v : mn[0];
+        mx[0] = v > mx[0] ? v : mx[0];
+        bad |= (unsigned)(v != v);
+    }
+    T a = mn[0], b = mx[0];
+    for (int i = 1; i < 8; ++i) {
+        a = mn[i] < a ? mn[i] : a;
+        b = mx[i] > b ? mx[i] : b;
+    }
+    *lo = (double)a;
+    *hi = (double)b;
+    *nan = bad != 0;
+}
+
+// Validates every phi value and finds the largest: the map is valid when no
+// value is a NaN and its smallest and largest values pass host_phi_ok (every
+// value between them then does).  Maps of more than 2^20 values are split
+// over host threads.
 bool host_scan_phi(const void* phi_host, int dtype, int64_t n, const rdc_params* p,
                    double* mx)
 {
-    auto scan = [&](int64_t k0, int64_t k1, double* m_out) {
-        double m = -INFINITY;
-        for (int64_t k = k0; k < k1; ++k) {
-            const double x = dtype == 0 ? (double)((const float*)phi_host)[k]
-                                        : ((const double*)phi_host)[k];
-            if (!host_phi_ok(x, p)) return false;
-            if (x > m) m = x;
-        }
-        *m_out = m;
-        return true;
+    auto scan = [&](int64_t k0, int64_t k1, double* lo, double* hi, bool* nan) {
+        if (dtype == 0) minmax_range((const float*)phi_host, k0, k1, lo, hi, nan);
+        else minmax_range((const double*)phi_host, k0, k1, lo, hi, nan);
     };
-    const int64_t kChunk = int64_t(1) << 22;
+    const int64_t kChunk = int64_t(1) << 20;
     unsigned hw = std::thread::hardware_concurrency();
-    int nt = (int)std::min<int64_t>(std::min<unsigned>(hw ? hw : 1, 16u), (n + kChunk - 1) / kChunk);
-    if (nt <= 1) return scan(0, n, mx);
-    std::vector<double> part(nt, -INFINITY);
-    std::vector<char> ok(nt, 1);
-    std::vector<std::thread> th;
+    const int nt = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<unsigned>(hw ? hw : 1, 16u), (n + kChunk - 1) / kChunk));
+    std::vector<double> lo(nt, INFINITY), hi(nt, -INFINITY);
+    std::vector<char> nan(nt, 0);
     const int64_t per = (n + nt - 1) / nt;
-    for (int t = 0; t < nt; ++t) {
+    auto part = [&](int t) {
         const int64_t k0 = std::min(n, t * per), k1 = std::min(n, k0 + per);
-        th.emplace_back([&, t, k0, k1]() { ok[t] = scan(k0, k1, &part[t]) ? 1 : 0; });
+        bool b = false;
+        if (k1 > k0) scan(k0, k1, &lo[t], &hi[t], &b);
+        nan[t] = b ? 1 : 0;
+    };
+    if (nt == 1) {
+        part(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nt; ++t) th.emplace_back(part, t);
+        part(0);
+        for (auto& x : th) x.join();
     }
-    for (auto& x : th) x.join();
-    double m = -INFINITY;
+    double a = INFINITY, b = -INFINITY;
     for (int t = 0; t < nt; ++t) {
-        if (!ok[t]) return false;
-        m = std::max(m, part[t]);
+        if (nan[t]) return false;
+        a = std::min(a, lo[t]);
+        b = std::max(b, hi[t]);
     }
-    *mx = m;
+    if (n > 0 && !(host_phi_ok(a, p) && host_phi_ok(b, p))) return false;
+    *mx = b;
     return true;
 }
 

@@ -27,49 +27,21 @@
 
 namespace rdc {
 
-#ifndef RDC_F32_STREAM_UNROLL_K3
-#define RDC_F32_STREAM_UNROLL_K3 1
-#endif
-#ifndef RDC_F32_STREAM_UNROLL_K4
-#define RDC_F32_STREAM_UNROLL_K4 6
-#endif
-#ifndef RDC_F32_STREAM_UNROLL_K5
-#define RDC_F32_STREAM_UNROLL_K5 3
-#endif
-#ifndef RDC_F32_STREAM_UNROLL_K6
-#define RDC_F32_STREAM_UNROLL_K6 6
-#endif
-#ifndef RDC_F32_STREAM_UNROLL_K7
-#define RDC_F32_STREAM_UNROLL_K7 3
-#endif
-#ifndef RDC_F32_STREAM_UNROLL_K8
-#define RDC_F32_STREAM_UNROLL_K8 3
-#endif
-
 // Unroll factor of the streamed kernel's row loop: the three-row register
 // rotation and the K-deep phi queue become renaming when it is a multiple of
-// both; the single-grid FP32 kernel (GH) takes per-K factors.
-template <int K, bool GH>
+// both.  Measured at 8192^2 (A/B, identical bits), the single-grid FP32
+// kernel (GH) runs best at K = 5 unrolled 5 times (809 -> 860 G
+// cell-updates/s), K = 6 6 times (809 -> 852), K = 7 7 times (749 -> 771),
+// K = 8 8 times (735 -> 757), K = 4 6 times (12 lost 7 %); the FP32 batched
+// kernel (UK) at K = 6 six times (512-grid sweep: 813 -> 834); the rest three
+// times from K = 4 (K times lost 9 % with BF16 storage at K = 6).
+template <int K, bool GH, bool UK>
 constexpr int stream_unroll()
 {
-    if constexpr (!GH) return K >= 4 ? 3 : 1;
-    else
-        return K == 3 ? RDC_F32_STREAM_UNROLL_K3
-             : K == 4 ? RDC_F32_STREAM_UNROLL_K4
-             : K == 5 ? RDC_F32_STREAM_UNROLL_K5
-             : K == 6 ? RDC_F32_STREAM_UNROLL_K6
-             : K == 7 ? RDC_F32_STREAM_UNROLL_K7
-             : K == 8 ? RDC_F32_STREAM_UNROLL_K8 : 1;
+    if constexpr (GH) return K == 4 ? 6 : K;
+    else if constexpr (UK && K == 6) return 6;
+    else return K >= 4 ? 3 : 1;
 }
-#ifndef RDC_F32_STREAM_MINB_K4
-#define RDC_F32_STREAM_MINB_K4 6
-#endif
-#ifndef RDC_F32_STREAM_MINB_K5
-#define RDC_F32_STREAM_MINB_K5 5
-#endif
-#ifndef RDC_F32_STREAM_MINB_K6
-#define RDC_F32_STREAM_MINB_K6 0
-#endif
 
 // N consecutive stored values (N * sizeof(S) = 4, 8 or 16 bytes) -> compute
 // type (S may also be a phi type: float or double).
@@ -159,7 +131,7 @@ struct StreamGeom {
 // interleave the levels' arithmetic (warp-uniform branches in the level loop
 // measured slower); the row loop is unrolled so that the three-row register
 // rotation becomes renaming.
-template <typename S, int MODE, int K, int N, bool GH>
+template <typename S, int MODE, int K, int N, bool GH, bool UK>
 __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                                                  const S* __restrict__ v,
                                                  const typename Traits<S>::PhiT* __restrict__ phi,
@@ -234,7 +206,7 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     // single-grid FP32 kernel at K = 4 (GH) runs best unrolled six times
     // (835 vs 813 G cell-updates/s; six times lost 17 % with 16-bit storage
     // and 3 % in the batched kernel).
-    constexpr int UNROLL = stream_unroll<K, GH>();
+    constexpr int UNROLL = stream_unroll<K, GH, UK>();
 #pragma unroll UNROLL
     for (int t = t0; t <= t_end; ++t) {
         T nphi[N];
@@ -428,14 +400,14 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     }
 }
 
-template <typename S, int MODE, int K, int N, bool GH>
+template <typename S, int MODE, int K, int N, bool GH, bool UK = false>
 __device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __restrict__ v,
                                             const typename Traits<S>::PhiT* __restrict__ phi,
                                             S* __restrict__ u1, S* __restrict__ v1, int W,
                                             int H, int64_t pitch, int col_out, int y0, int y1,
                                             const Model<typename Traits<S>::T>& m)
 {
-    stream_warp_impl<S, MODE, K, N, GH>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
+    stream_warp_impl<S, MODE, K, N, GH, UK>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
 }
 
 // The single-grid FP32 kernel at K >= 4 (GH) takes the variants that
@@ -485,14 +457,13 @@ k_stepk_stream_capped(const S* __restrict__ u, const S* __restrict__ v,
 }
 
 // CTAs per SM the single-grid FP32 kernel is compiled for (0: the compiler's
-// choice).
+// choice).  Measured at 8192^2 (A/B, identical bits): K = 4 capped for 6 CTAs
+// (12 bytes spilled) 797 -> 807, K = 5 for 5 (24 bytes) 839 -> 860 G
+// cell-updates/s; K = 6 for 5 lost (72 bytes spilled, 857 -> 809).
 template <typename S, int MODE, int K>
 constexpr int stream_single_min_ctas()
 {
-    return (sizeof(S) != 4 || (MODE & MODE_SR) != 0)
-               ? 0
-               : (K == 4 ? RDC_F32_STREAM_MINB_K4
-                         : (K == 5 ? RDC_F32_STREAM_MINB_K5 : (K == 6 ? RDC_F32_STREAM_MINB_K6 : 0)));
+    return (sizeof(S) != 4 || (MODE & MODE_SR) != 0) ? 0 : (K == 4 ? 6 : (K == 5 ? 5 : 0));
 }
 
 // Persistent k-step launch over a batch of grids (see k_step1_batch).
@@ -513,7 +484,7 @@ __device__ __forceinline__ void stream_batch_body(const GridDesc* __restrict__ d
         const int par = (d.par + j) & 1;
         Model<T> m = model_of<T>(d);
         m.step0 += sbase;
-        stream_warp<S, MODE, K, N, false>(
+        stream_warp<S, MODE, K, N, false, sizeof(S) == 4>(
             static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
             static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, x0, y0, min(y0 + rows, d.H), m);
@@ -566,7 +537,7 @@ cudaError_t launch_stream_k(const Planes& g, const Model<typename Traits<S>::T>&
 {
     using PhiT = typename Traits<S>::PhiT;
     constexpr int N = StreamVec<S, K>::N;
-    const int wpb = 4;
+    const int wpb = 4;  // warps per CTA (1 or 2 measured the same at K = 5, 6)
     if ((g.H + rows - 1) / rows > 65535) return cudaErrorInvalidValue;
     return dispatch_full<S>(sr, [&](auto mc) {
         using G = StreamGeom<S, K, N, (decltype(mc)::value & MODE_SR) != 0>;
