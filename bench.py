@@ -383,8 +383,9 @@ def main():
     if rank == 0 and not args.no_extras:
         # temporal blocking and storage modes: effective GCUPS on the same grid
         tb = {"1": _mode_gcups(pkg, stream, "f32", 1, 1000)}
-        for k in (2, 3, 4, 6, 8):
-            tb[str(k)] = max(_mode_gcups(pkg, stream, "f32", k, 960, krows=kr) for kr in (64, 128))
+        for k in (2, 3, 4, 5, 6, 7, 8):
+            tb[str(k)] = max(_mode_gcups(pkg, stream, "f32", k, 960 // k * k, krows=kr)
+                             for kr in (64, 128))
         tuned = _tuned(pkg, stream, "f32")
         modes = {m: _mode_gcups(pkg, stream, m, 1, 1000) for m in ("bf16", "f16")}
         modes["bf16_tuned"] = _tuned(pkg, stream, "bf16")

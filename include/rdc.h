@@ -418,7 +418,7 @@ typedef struct {
 
 /*
  * Autotuner: times reps launches of each candidate shape (single step with
- * 4..32 rows per CTA; k in {2, 3, 4, 6, 8} with the register-streamed kernel
+ * 4..32 rows per CTA; k in {2, ..., 8} with the register-streamed kernel
  * at 32..256 rows per CTA -- full model only -- and with the shared-memory
  * tile kernel; on grids so tall that a shape would need more than 65535 CTA
  * rows, that shape is skipped), keeps the fastest in cell-updates per second
@@ -591,7 +591,7 @@ int rdc_batch_stability(rdc_batch* b, int32_t idx, double* rho);
 
 /*
  * Autotuner: times reps launches of each candidate (single step with 8, 16 or
- * 32 rows per item; k in {2, 3, 4, 6, 8} with 32..256 rows per item) over all
+ * 32 rows per item; k in {2, 3, 4, 5, 6, 8} with 32..256 rows per item) over all
  * live grids, keeps the fastest in cell-updates per second, and reports it in
  * *out (optional).  Every timed launch reads the current buffers and writes
  * the spare ones, so tuning does not advance or change any grid's state.

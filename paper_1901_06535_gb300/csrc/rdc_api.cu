@@ -1019,7 +1019,7 @@ int rdc_tune(rdc_sim* s, int32_t reps, rdc_launch_shape* out, double* best_gcups
     ShapeK k1 = s->shapek;
     k1.k = 1;
     for (int rows : {4, 8, 16, 32}) cands.push_back({false, Shape1{s->shape1.bx, rows}, k1});
-    for (int k : {2, 3, 4, 6, 8}) {
+    for (int k : {2, 3, 4, 5, 6, 7, 8}) {
         if (s->mode == MODE_FULL)  // the streamed kernel serves the full model only
             for (int krows : {32, 64, 128, 256})
                 cands.push_back({true, s->shape1, ShapeK{64, 32, k, 256, 0, krows}});

@@ -730,7 +730,7 @@ int rdc_batch_tune(rdc_batch* b, int32_t reps, rdc_batch_info* out)
     struct Cand { int k, rows, krows; };
     std::vector<Cand> cands;
     for (int rows : {8, 16, 32}) cands.push_back({1, rows, saved.krows});
-    for (int k : {2, 3, 4, 6, 8})
+    for (int k : {2, 3, 4, 5, 6, 8})
         for (int krows : {32, 64, 128, 256}) cands.push_back({k, saved.rows, krows});
     for (const Cand& c : cands) {
         b->cfg.k = c.k;
