@@ -42,6 +42,12 @@ def test_native_bench_json_line():
     # health check per bench step
     assert line["gpu_launches"] == 2 * (40 + 200 + 1)
     for key in ("temporal_blocking_gcups", "storage_modes_gcups", "batch_sweep", "serving",
-                "render"):
+                "serving_loaded", "render"):
         assert key in line, key
     assert line["serving"]["frames"] == 64 * 100 and line["serving"]["p99_ms"] > 0
+    ld = line["serving_loaded"]
+    assert ld["frames"] == 64 * 180 and ld["peak_sessions"] == 64 and ld["p99_ms"] > 0
+    sw = line["batch_sweep"]
+    assert sw["gcups_healthy_grids_only"] <= sw["gcups"]
+    assert set(sw["first_bad"]) == {str(i) for i in sw["unhealthy_grids"]}
+    assert set(line["temporal_blocking_gcups"]) == {str(k) for k in range(1, 9)}
