@@ -530,11 +530,18 @@ int rdc_batch_create(int32_t n, const rdc_grid* grids, const rdc_params* params,
                      const float* const* phi_host, void* stream, rdc_batch** out);
 
 /* Adds one grid (allocates its planes; rest state) and returns its index in
- * *idx (a freed slot is reused).  RDC_ENOMEM if the device memory is short. */
+ * *idx (a freed slot is reused).  The host map is validated and copied before
+ * the call returns; nothing waits for the device: the planes come from the
+ * batch's stream-ordered memory pool and their initialisation (phi upload,
+ * rest state) is enqueued on the batch's stream behind the work already there
+ * (from page-locked host memory the map's copy is asynchronous too).
+ * RDC_ENOMEM if the device memory is short. */
 int rdc_batch_add(rdc_batch* b, rdc_grid g, const rdc_params* p, const float* phi_host,
                   int32_t* idx);
 
-/* Removes grid idx and frees its memory (waits for the batch's stream). */
+/* Removes grid idx; its memory returns to the batch's pool once the work
+ * enqueued on the batch's stream before this call has finished (the call does
+ * not wait), and the slot can take a new grid at once. */
 int rdc_batch_remove(rdc_batch* b, int32_t idx);
 
 /* Waits for the batch's stream, frees everything.  NULL is a no-op. */
@@ -554,10 +561,11 @@ int rdc_batch_set_state(rdc_batch* b, int32_t idx, const void* u_host, const voi
 /*
  * Async.  Advances the m grids idx[0..m-1] (distinct, live; idx = NULL: every
  * live grid) by n >= 0 Euler steps: n / k launches of the k-step kernel and
- * n % k single-step launches, each a persistent launch over warp-sized work
- * items of all those grids.  With graphs on (the default) the launch sequence
- * for a given (subset, n, shape) is captured once into a CUDA graph and
- * replayed afterwards.
+ * n % k single-step launches, each a persistent launch over the warp-sized
+ * tiles of exactly those grids (the call's tile map, uploaded on the batch's
+ * stream).  With graphs on (the default) the launch sequence for a given
+ * (n, shape) is captured once into a CUDA graph and replayed for any subset;
+ * adding or removing a grid discards the graphs.
  */
 int rdc_batch_step(rdc_batch* b, const int32_t* idx, int32_t m, int64_t n);
 
