@@ -358,3 +358,36 @@ def test_unusable_device_is_reported_not_hidden(librdc):
     bad.dt = -1.0
     assert L.rdc_create(rdc_grid(16, 16), ctypes.byref(bad), None, None,
                         ctypes.byref(h)) == librdc.RDC_EINVAL
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """Every structure the binding passes through the C ABI has the header's
+    size and field offsets (the header compiled by the host C compiler)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1901_06535_gb300 import _capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = [_capi.rdc_grid, _capi.rdc_params, _capi.rdc_view, _capi.rdc_launch_shape,
+               _capi.rdc_batch_info, _capi.rdc_division_report]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rdc.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(out[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(out[f"{n}.{f}"]) == getattr(st, f).offset, (n, f)
