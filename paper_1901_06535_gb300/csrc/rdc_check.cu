@@ -19,6 +19,7 @@
 //       long overflowed anyway) -- div_rn and the paired div2_rn,
 //   [2] random normal operand pairs (a counter-based SplitMix64 stream).
 #include <cmath>
+#include <type_traits>
 
 #include "rdc.h"
 #include "rdc_device.cuh"
@@ -144,8 +145,19 @@ __global__ void k_sr_sample(const float* __restrict__ x, int n, unsigned seed, l
     if (i >= n) return;
     const int col = col0 + i;
     const unsigned w = sr_word(sr_quad_bits(seed, col >> 2, row, step), col & 3);
-    uo[i] = quantize_sr<S>(x[i], w);
-    vo[i] = quantize_sr<S>(x[i], w << 16);
+    // the forms the step kernels take: the integer ones where they apply
+    // (BF16 unless NaN, FP16 in its normal range), the general one otherwise
+    const float xi = x[i];
+    if (std::is_same_v<S, __nv_bfloat16> && !isnan(xi)) {
+        uo[i] = sr_bf16(xi, w >> 16);
+        vo[i] = sr_bf16(xi, w & 0xFFFFu);
+    } else if (std::is_same_v<S, __half> && fp16_normal(xi)) {
+        uo[i] = sr_f16_normal(xi, w >> 16);
+        vo[i] = sr_f16_normal(xi, w & 0xFFFFu);
+    } else {
+        uo[i] = quantize_sr<S>(xi, w);
+        vo[i] = quantize_sr<S>(xi, w << 16);
+    }
 }
 
 // Philox4x32-10 outputs for n given counters and keys, computed by the very

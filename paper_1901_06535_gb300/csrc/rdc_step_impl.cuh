@@ -138,7 +138,9 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
             // words take the upper halves of the sums directly) unless the
             // quad holds a NaN, which the paired sum of its values exposes (an
             // infinity of each sign also sends the quad to the general form,
-            // which is exact for every value); FP16 the general form.
+            // which is exact for every value); FP16 takes it (sr_f16_normal)
+            // when all eight values lie in FP16's normal range, else the
+            // general form.
             if (act) {
                 unsigned pu[VEC / 2], pv[VEC / 2];
 #pragma unroll
@@ -176,6 +178,18 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
                                                sr_bf16_carry(b2.y, w[1] & 0xFFFFu));
                         pv[e / 2 + 1] = pack_upper(sr_bf16_carry(d2.x, w[2] & 0xFFFFu),
                                                    sr_bf16_carry(d2.y, w[3] & 0xFFFFu));
+                    } else if (std::is_same_v<S, __half> &&
+                               fp16_normal(a2.x) && fp16_normal(a2.y) && fp16_normal(b2.x) &&
+                               fp16_normal(b2.y) && fp16_normal(c2.x) && fp16_normal(c2.y) &&
+                               fp16_normal(d2.x) && fp16_normal(d2.y)) {
+                        pu[e / 2] = pack(sr_f16_normal(a2.x, w[0] >> 16),
+                                         sr_f16_normal(a2.y, w[1] >> 16));
+                        pu[e / 2 + 1] = pack(sr_f16_normal(c2.x, w[2] >> 16),
+                                             sr_f16_normal(c2.y, w[3] >> 16));
+                        pv[e / 2] = pack(sr_f16_normal(b2.x, w[0] & 0xFFFFu),
+                                         sr_f16_normal(b2.y, w[1] & 0xFFFFu));
+                        pv[e / 2 + 1] = pack(sr_f16_normal(d2.x, w[2] & 0xFFFFu),
+                                             sr_f16_normal(d2.y, w[3] & 0xFFFFu));
                     } else {
                         pu[e / 2] = pack(quantize_sr<S>(a2.x, w[0]), quantize_sr<S>(a2.y, w[1]));
                         pu[e / 2 + 1] = pack(quantize_sr<S>(c2.x, w[2]), quantize_sr<S>(c2.y, w[3]));

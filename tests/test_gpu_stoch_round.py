@@ -29,6 +29,10 @@ def _values(rng, n):
     mag = np.exp(rng.uniform(np.log(1e-6), np.log(6e4), n)).astype(np.float32)
     x = mag * rng.choice(np.array([-1, 1], dtype=np.float32), n)
     x[:8] = [0.0, -0.0, 0.3, 0.5, 65504.0, 65510.0, 1e-7, -2.5e-5]
+    # the edges of FP16's normal range and values just inside and outside them
+    tiny = np.float32(2.0 ** -14)
+    x[8:16] = [tiny, np.nextafter(tiny, np.float32(0)), np.nextafter(tiny, np.float32(1)),
+               -tiny, 65503.0, -65503.99, np.float32(65472.5), np.float32(3.3e38)]
     return x
 
 
