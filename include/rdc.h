@@ -269,6 +269,41 @@ int rdc_check(rdc_sim* sim, int64_t* first_bad);
  * (as double).  Any index outside [0, W*H) gives RDC_EINVAL. */
 int rdc_probe(rdc_sim* sim, int32_t n, const int64_t* cells, double* out);
 
+/*
+ * Halo rows of a row-strip split of one grid.  In Eq. 1 only the Laplacian
+ * of u couples a row to its neighbours (v has no diffusion term and phi is
+ * static), so a grid can be cut into strips of rows, each a simulation of
+ * its own that holds its rows plus h halo rows copied from each neighbour:
+ * stepping a strip n <= h times leaves its own rows exactly as the whole
+ * grid would have them (the cut edge, a mirror border, corrupts one halo row
+ * per step), and the neighbours then exchange h rows of u and v again.  The
+ * paper runs one device and has no such split; these two calls are the
+ * copies of that exchange.  Bitwise equality with the unsplit grid needs the
+ * rows' own operation sequence, which every storage type has except under
+ * RDC_STOCH_ROUND (its random words are keyed by the row index in the
+ * strip).
+ *
+ * Async (enqueued on the simulation's stream; with pageable host memory the
+ * runtime may complete the copy before returning).
+ * rdc_get_rows copies rows [row0, row0 + nrows) of the current u and v into
+ * u_dst and v_dst; rdc_put_rows writes them from u_src and v_src.
+ *   u_*, v_* : device, pinned or pageable host memory (any pointer the
+ *              runtime's unified addressing resolves), in the simulation's
+ *              storage type (rdc_view.elem_bytes per value); either may be
+ *              NULL to skip that plane.
+ *   pitch_bytes : row stride of those buffers; 0 = packed (W * elem_bytes).
+ *              A destination simulation's plane (rdc_view u/v plus
+ *              row * pitch_bytes) is a valid buffer: it is current until
+ *              that simulation's next rdc_step, so both simulations must
+ *              share a stream (or the caller orders the two streams).
+ * RDC_EINVAL: sim NULL; row0 < 0; nrows < 0; row0 + nrows > H; a nonzero
+ * pitch_bytes below W * elem_bytes.  nrows = 0 does nothing.
+ */
+int rdc_get_rows(rdc_sim* sim, int32_t row0, int32_t nrows, void* u_dst, void* v_dst,
+                 size_t pitch_bytes);
+int rdc_put_rows(rdc_sim* sim, int32_t row0, int32_t nrows, const void* u_src,
+                 const void* v_src, size_t pitch_bytes);
+
 /* ---- drawing substrate (§3) ---------------------------------------------- */
 /* Line width presets of §3, in cells (one pixel of the paper's simulation is
  * one cell): permeable lines slow waves, semi-permeable lines pass waves that

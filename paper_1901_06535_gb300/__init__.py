@@ -26,7 +26,8 @@ from ._capi import (  # noqa: F401  (re-exported C-ABI names)
     RDC_SNAP_DEGREES, RDC_WIDTH_IMPERMEABLE, RDC_WIDTH_PERMEABLE, RDC_WIDTH_SEMIPERMEABLE,
     rdc_draw_line, rdc_fill_phi, rdc_read_phi, rdc_snap_segment, rdc_check_division,
     rdc_division_report, RDC_STOCH_ROUND, rdc_stoch_round_sample, rdc_set_step_index,
-    rdc_batch_set_step_index, rdc_philox_sample, rdc_batch_stability)
+    rdc_batch_set_step_index, rdc_philox_sample, rdc_batch_stability, rdc_get_rows,
+    rdc_put_rows)
 
 
 class Sim:

@@ -131,6 +131,8 @@ _SIGS = {
     "rdc_read": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     "rdc_check": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "rdc_probe": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "rdc_get_rows": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_size_t]),
+    "rdc_put_rows": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_size_t]),
     "rdc_sync": (ctypes.c_int, [_P]),
     "rdc_rest_state": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_double)]),
@@ -409,6 +411,48 @@ def rdc_probe(h, cells) -> np.ndarray:
     out = np.empty(c.size, dtype=np.float64)
     _chk(lib().rdc_probe(h, c.size, c.ctypes.data, out.ctypes.data), "rdc_probe")
     return out
+
+
+def _rows_buf(x, nbytes: int, elem_bytes: int, name: str):
+    """Address of a row buffer: an int (device or host pointer), an object
+    with data_ptr() (a torch tensor), or a C-contiguous numpy array of the
+    storage element size holding at least nbytes."""
+    if x is None:
+        return None
+    if isinstance(x, (int, np.integer)):
+        return int(x)
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous or x.dtype.itemsize != elem_bytes or x.nbytes < nbytes:
+            raise ValueError(f"{name}: need a C-contiguous array of {elem_bytes}-byte elements "
+                             f"holding {nbytes} bytes")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"{name}: pointer, numpy array or tensor expected")
+
+
+def _rows_call(fn, h, row0, nrows, u, v, pitch_bytes, what):
+    view = rdc_get_view(h)
+    row = int(pitch_bytes) or view.width * view.elem_bytes
+    need = max(int(nrows) - 1, 0) * row + view.width * view.elem_bytes if nrows > 0 else 0
+    pu = _rows_buf(u, need, view.elem_bytes, "u")
+    pv = _rows_buf(v, need, view.elem_bytes, "v")
+    _chk(fn(h, int(row0), int(nrows), pu, pv, int(pitch_bytes)), what)
+    if isinstance(u, np.ndarray) or isinstance(v, np.ndarray):
+        rdc_sync(h)  # a host array is complete (get) or free to reuse (put) on return
+
+
+def rdc_get_rows(h, row0: int, nrows: int, u_dst=None, v_dst=None, pitch_bytes: int = 0):
+    """Copies rows [row0, row0 + nrows) of the current u and v into u_dst and
+    v_dst (storage type; pitch_bytes 0 = packed rows).  Buffers are pointers
+    (ints), tensors, or numpy arrays (then the call waits for the copy)."""
+    _rows_call(lib().rdc_get_rows, h, row0, nrows, u_dst, v_dst, pitch_bytes, "rdc_get_rows")
+
+
+def rdc_put_rows(h, row0: int, nrows: int, u_src=None, v_src=None, pitch_bytes: int = 0):
+    """Writes rows [row0, row0 + nrows) of the current u and v from u_src and
+    v_src (the layout of rdc_get_rows)."""
+    _rows_call(lib().rdc_put_rows, h, row0, nrows, u_src, v_src, pitch_bytes, "rdc_put_rows")
 
 
 def rdc_sync(h) -> int:

@@ -780,6 +780,48 @@ int rdc_read(rdc_sim* s, void* u_out, void* v_out, int32_t dtype)
     return rdc_check(s, nullptr);
 }
 
+// Copies rows of the current u and v planes to (get) or from (put) caller
+// buffers of the storage type, one 2-D copy per plane on the sim's stream.
+static int copy_rows(rdc_sim* s, int32_t row0, int32_t nrows, void* const bufs[2],
+                     size_t pitch_bytes, bool get)
+{
+    if (!s || row0 < 0 || nrows < 0 || (int64_t)row0 + nrows > s->H) return RDC_EINVAL;
+    const size_t esz = (size_t)state_bytes(s->prec);
+    const size_t row_bytes = (size_t)s->W * esz;
+    if (pitch_bytes == 0) pitch_bytes = row_bytes;
+    if (pitch_bytes < row_bytes) return RDC_EINVAL;
+    if (nrows == 0) return RDC_OK;
+    void* planes[2] = {s->u[s->cur], s->v[s->cur]};
+    const size_t plane_pitch = (size_t)s->pitch * esz;
+    for (int b = 0; b < 2; ++b) {
+        if (!bufs[b]) continue;
+        char* rows = (char*)planes[b] + (size_t)row0 * plane_pitch;
+        if (get)
+            CK(cudaMemcpy2DAsync(bufs[b], pitch_bytes, rows, plane_pitch, row_bytes, nrows,
+                                 cudaMemcpyDefault, s->stream),
+               "cudaMemcpy2DAsync(get rows)");
+        else
+            CK(cudaMemcpy2DAsync(rows, plane_pitch, bufs[b], pitch_bytes, row_bytes, nrows,
+                                 cudaMemcpyDefault, s->stream),
+               "cudaMemcpy2DAsync(put rows)");
+    }
+    return RDC_OK;
+}
+
+int rdc_get_rows(rdc_sim* s, int32_t row0, int32_t nrows, void* u_dst, void* v_dst,
+                 size_t pitch_bytes)
+{
+    void* bufs[2] = {u_dst, v_dst};
+    return copy_rows(s, row0, nrows, bufs, pitch_bytes, true);
+}
+
+int rdc_put_rows(rdc_sim* s, int32_t row0, int32_t nrows, const void* u_src,
+                 const void* v_src, size_t pitch_bytes)
+{
+    void* bufs[2] = {const_cast<void*>(u_src), const_cast<void*>(v_src)};
+    return copy_rows(s, row0, nrows, bufs, pitch_bytes, false);
+}
+
 int rdc_probe(rdc_sim* s, int32_t n, const int64_t* cells, double* out)
 {
     if (!s || n < 0 || (n > 0 && (!cells || !out))) return RDC_EINVAL;

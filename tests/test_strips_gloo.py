@@ -7,7 +7,10 @@
    oracle bit for bit -- the exchange a multi-GPU strip path would need.
 2. The same with temporal blocking: K rows of u and v every K steps, the
    halo recomputed (K = 4, 6).
-3. The benchmark's rank aggregation: the slowest rank's time and the
+3. The library's strip plan (paper_1901_06535_gb300.strips.strip_plan) on
+   three ranks: its copies become send/recv pairs between the ranks that
+   hold the strips, and the gathered strips equal the unsplit oracle.
+4. The benchmark's rank aggregation: the slowest rank's time and the
    whole-job (weak-scaling) rate.
 """
 from __future__ import annotations
@@ -166,6 +169,71 @@ def test_kblocked_strips_equal_unsplit(tmp_path, K):
                        join=True, start_method="spawn")
     orc, phi, u, v = _initial()
     ref = orc.run(phi, u, v, STEPS)
+    got = np.load(out)
+    assert np.array_equal(got["u"], ref["u"]) and np.array_equal(got["v"], ref["v"])
+
+
+def _plan_worker(rank, world, port, out_path, halo, steps):
+    """One strip per rank, exchanged as strip_plan's copies say: a copy whose
+    sender is this rank is a send, one whose receiver is this rank a receive."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1901_06535_gb300.strips import strip_plan
+    orc, phi, u, v = _initial()
+    strips, transfers = strip_plan(H, world, halo)
+    me = strips[rank]
+    us, vs = u[me.e0:me.e1].copy(), v[me.e0:me.e1].copy()
+    ph = np.ascontiguousarray(phi[me.e0:me.e1])
+    left = steps
+    while left > 0:
+        m = min(left, halo)
+        reqs, recvd = [], []
+        for t in transfers:
+            if t.src == rank:
+                for a in (us, vs):
+                    reqs.append(dist.isend(torch.from_numpy(
+                        a[t.src_row:t.src_row + t.nrows].ravel().copy()), t.dst))
+            if t.dst == rank:
+                bufs = [torch.empty(t.nrows * W, dtype=torch.float64) for _ in range(2)]
+                for b in bufs:
+                    reqs.append(dist.irecv(b, t.src))
+                recvd.append((t, bufs))
+        for q in reqs:
+            q.wait()
+        for t, (bu, bv) in recvd:
+            us[t.dst_row:t.dst_row + t.nrows] = bu.numpy().reshape(t.nrows, W)
+            vs[t.dst_row:t.dst_row + t.nrows] = bv.numpy().reshape(t.nrows, W)
+        out = orc.run(ph, us, vs, m)
+        us, vs = out["u"], out["v"]
+        left -= m
+    own_u = np.ascontiguousarray(us[me.r0 - me.e0:me.r1 - me.e0])
+    own_v = np.ascontiguousarray(vs[me.r0 - me.e0:me.r1 - me.e0])
+    if rank == 0:
+        parts_u, parts_v = [own_u], [own_v]
+        for src in range(1, world):
+            n = (strips[src].r1 - strips[src].r0) * W
+            tu = torch.empty(n, dtype=torch.float64)
+            tv = torch.empty(n, dtype=torch.float64)
+            dist.recv(tu, src)
+            dist.recv(tv, src)
+            parts_u.append(tu.numpy().reshape(-1, W))
+            parts_v.append(tv.numpy().reshape(-1, W))
+        np.savez(out_path, u=np.concatenate(parts_u), v=np.concatenate(parts_v))
+    else:
+        dist.send(torch.from_numpy(own_u.ravel().copy()), 0)
+        dist.send(torch.from_numpy(own_v.ravel().copy()), 0)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("halo,steps", [(3, 47), (5, 60)])
+def test_strip_plan_on_three_ranks_equals_unsplit(tmp_path, halo, steps):
+    out = str(tmp_path / f"plan{halo}.npz")
+    mp.start_processes(_plan_worker, args=(3, _free_port(), out, halo, steps), nprocs=3,
+                       join=True, start_method="spawn")
+    orc, phi, u, v = _initial()
+    ref = orc.run(phi, u, v, steps)
     got = np.load(out)
     assert np.array_equal(got["u"], ref["u"]) and np.array_equal(got["v"], ref["v"])
 
