@@ -91,6 +91,110 @@ constexpr int step1_vec()
     return ((MODE & MODE_SR) != 0 && sizeof(S) == 2) ? 4 : Traits<S>::VEC;
 }
 
+// One row of a lane's VEC cells (VEC / 4 whole quads) of a single Euler step
+// under stochastic rounding: the cell updates from the north, centre and south
+// rows of u (un, uc, us; wl, er: the cells west and east of the lane's span),
+// v and phi of the row, then u' and v' of row r rounded stochastically to S
+// and stored at ro + col0.  16-bit storage, one quad at a time -- its two cell
+// pairs, its random words, its rounding, its packed words -- so that only one
+// quad's values are live at once.  BF16 takes the add-and-carry form of the
+// rule (sr_bf16; the packed words take the upper halves of the sums directly)
+// unless the quad holds a NaN, which the paired sum of its values exposes (an
+// infinity of each sign also sends the quad to the general form, which is
+// exact for every value); FP16 takes it (sr_f16_normal) when all eight values
+// lie in FP16's normal range, else the general form.
+template <typename S, int MODE, int VEC>
+__device__ __forceinline__ void sr_row(const float (&un)[VEC], const float (&uc)[VEC],
+                                       const float (&us)[VEC], const float (&vv)[VEC],
+                                       const float (&ph)[VEC], float wl, float er, int col0,
+                                       int W, int r, int64_t ro, S* __restrict__ u1,
+                                       S* __restrict__ v1, const Model<float>& m)
+{
+    static_assert(sizeof(S) == 2 && VEC % 4 == 0, "16-bit storage, whole quads");
+    unsigned pu[VEC / 2], pv[VEC / 2];
+#pragma unroll
+    for (int e = 0; e < VEC; e += 4) {
+        float2 a2, b2, c2, d2;   // u', v' of cells e, e+1 and e+2, e+3
+#pragma unroll
+        for (int h = 0; h < 4; h += 2) {
+            const int x = e + h;
+            const float c0 = uc[x], c1 = uc[x + 1];
+            const float2 w2 = make_float2((x == 0) ? wl : uc[x - 1], c0);
+            const float2 e2 = make_float2(col0 + x >= W - 1 ? c0 : c1,
+                                          col0 + x + 1 >= W - 1
+                                              ? c1
+                                              : ((x + 2 == VEC) ? er : uc[x + 2]));
+            cell_update2<MODE>(make_float2(c0, c1), w2, e2,
+                               make_float2(un[x], un[x + 1]),
+                               make_float2(us[x], us[x + 1]),
+                               make_float2(vv[x], vv[x + 1]),
+                               make_float2(ph[x], ph[x + 1]), m, h ? c2 : a2,
+                               h ? d2 : b2);
+        }
+        const Philox4 rb = sr_quad_bits(m.seed, (col0 + e) >> 2, r, m.step0 + 1);
+        const float2 chk = __fadd2_rn(__fadd2_rn(a2, b2), __fadd2_rn(c2, d2));
+        const unsigned w[4] = {rb.x, rb.y, rb.z, rb.w};
+        auto pack = [](float a, float b) {
+            if constexpr (std::is_same_v<S, __nv_bfloat16>) return f2_to_bf2(a, b);
+            else return f2_to_h2(a, b);
+        };
+        if (std::is_same_v<S, __nv_bfloat16> && !(isnan(chk.x) || isnan(chk.y))) {
+            pu[e / 2] = pack_upper(sr_bf16_carry(a2.x, w[0] >> 16),
+                                   sr_bf16_carry(a2.y, w[1] >> 16));
+            pu[e / 2 + 1] = pack_upper(sr_bf16_carry(c2.x, w[2] >> 16),
+                                       sr_bf16_carry(c2.y, w[3] >> 16));
+            pv[e / 2] = pack_upper(sr_bf16_carry(b2.x, w[0] & 0xFFFFu),
+                                   sr_bf16_carry(b2.y, w[1] & 0xFFFFu));
+            pv[e / 2 + 1] = pack_upper(sr_bf16_carry(d2.x, w[2] & 0xFFFFu),
+                                       sr_bf16_carry(d2.y, w[3] & 0xFFFFu));
+        } else if (std::is_same_v<S, __half> &&
+                   fp16_normal(a2.x) && fp16_normal(a2.y) && fp16_normal(b2.x) &&
+                   fp16_normal(b2.y) && fp16_normal(c2.x) && fp16_normal(c2.y) &&
+                   fp16_normal(d2.x) && fp16_normal(d2.y)) {
+            pu[e / 2] = pack(sr_f16_normal(a2.x, w[0] >> 16),
+                             sr_f16_normal(a2.y, w[1] >> 16));
+            pu[e / 2 + 1] = pack(sr_f16_normal(c2.x, w[2] >> 16),
+                                 sr_f16_normal(c2.y, w[3] >> 16));
+            pv[e / 2] = pack(sr_f16_normal(b2.x, w[0] & 0xFFFFu),
+                             sr_f16_normal(b2.y, w[1] & 0xFFFFu));
+            pv[e / 2 + 1] = pack(sr_f16_normal(d2.x, w[2] & 0xFFFFu),
+                                 sr_f16_normal(d2.y, w[3] & 0xFFFFu));
+        } else {
+            pu[e / 2] = pack(quantize_sr<S>(a2.x, w[0]), quantize_sr<S>(a2.y, w[1]));
+            pu[e / 2 + 1] = pack(quantize_sr<S>(c2.x, w[2]), quantize_sr<S>(c2.y, w[3]));
+            pv[e / 2] = pack(quantize_sr<S>(b2.x, w[0] << 16),
+                             quantize_sr<S>(b2.y, w[1] << 16));
+            pv[e / 2 + 1] = pack(quantize_sr<S>(d2.x, w[2] << 16),
+                                 quantize_sr<S>(d2.y, w[3] << 16));
+        }
+    }
+    if (col0 + VEC <= W) {
+        if constexpr (VEC == 8) {
+            st16(u1 + ro + col0, make_uint4(pu[0], pu[1], pu[2], pu[3]));
+            st16(v1 + ro + col0, make_uint4(pv[0], pv[1], pv[2], pv[3]));
+        } else {
+            *reinterpret_cast<uint2*>(u1 + ro + col0) = make_uint2(pu[0], pu[1]);
+            *reinterpret_cast<uint2*>(v1 + ro + col0) = make_uint2(pv[0], pv[1]);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            if (col0 + e < W) {
+                const int sh = 16 * (e & 1);
+                const unsigned short hu = (unsigned short)(pu[e / 2] >> sh);
+                const unsigned short hv = (unsigned short)(pv[e / 2] >> sh);
+                if constexpr (std::is_same_v<S, __nv_bfloat16>) {
+                    u1[ro + col0 + e] = __ushort_as_bfloat16(hu);
+                    v1[ro + col0 + e] = __ushort_as_bfloat16(hv);
+                } else {
+                    u1[ro + col0 + e] = __ushort_as_half(hu);
+                    v1[ro + col0 + e] = __ushort_as_half(hv);
+                }
+            }
+        }
+    }
+}
+
 // One warp's share of a single Euler step: 32 vectors of VEC cells starting
 // at column wcol0, rows [row0, row1).  Warps are independent (no shared
 // memory, no block barrier), so the same body serves one grid per launch
@@ -131,100 +235,7 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
         if (lane != 0) wl = wsh;
         if (lane != 31) er = esh;
         if constexpr ((MODE & MODE_SR) != 0) {
-            // 16-bit storage with stochastic rounding, one quad at a time --
-            // its two cell pairs, its random words, its rounding, its packed
-            // words -- so that only one quad's values are live at once.  BF16
-            // takes the add-and-carry form of the rule (sr_bf16; the packed
-            // words take the upper halves of the sums directly) unless the
-            // quad holds a NaN, which the paired sum of its values exposes (an
-            // infinity of each sign also sends the quad to the general form,
-            // which is exact for every value); FP16 takes it (sr_f16_normal)
-            // when all eight values lie in FP16's normal range, else the
-            // general form.
-            if (act) {
-                unsigned pu[VEC / 2], pv[VEC / 2];
-#pragma unroll
-                for (int e = 0; e < VEC; e += 4) {
-                    float2 a2, b2, c2, d2;   // u', v' of cells e, e+1 and e+2, e+3
-#pragma unroll
-                    for (int h = 0; h < 4; h += 2) {
-                        const int x = e + h;
-                        const float c0 = uc[x], c1 = uc[x + 1];
-                        const float2 w2 = make_float2((x == 0) ? wl : uc[x - 1], c0);
-                        const float2 e2 = make_float2(col0 + x >= W - 1 ? c0 : c1,
-                                                      col0 + x + 1 >= W - 1
-                                                          ? c1
-                                                          : ((x + 2 == VEC) ? er : uc[x + 2]));
-                        cell_update2<MODE>(make_float2(c0, c1), w2, e2,
-                                           make_float2(un[x], un[x + 1]),
-                                           make_float2(us[x], us[x + 1]),
-                                           make_float2(vv[x], vv[x + 1]),
-                                           make_float2(ph[x], ph[x + 1]), m, h ? c2 : a2,
-                                           h ? d2 : b2);
-                    }
-                    const Philox4 rb = sr_quad_bits(m.seed, (col0 + e) >> 2, r, m.step0 + 1);
-                    const float2 chk = __fadd2_rn(__fadd2_rn(a2, b2), __fadd2_rn(c2, d2));
-                    const unsigned w[4] = {rb.x, rb.y, rb.z, rb.w};
-                    auto pack = [](float a, float b) {
-                        if constexpr (std::is_same_v<S, __nv_bfloat16>) return f2_to_bf2(a, b);
-                        else return f2_to_h2(a, b);
-                    };
-                    if (std::is_same_v<S, __nv_bfloat16> && !(isnan(chk.x) || isnan(chk.y))) {
-                        pu[e / 2] = pack_upper(sr_bf16_carry(a2.x, w[0] >> 16),
-                                               sr_bf16_carry(a2.y, w[1] >> 16));
-                        pu[e / 2 + 1] = pack_upper(sr_bf16_carry(c2.x, w[2] >> 16),
-                                                   sr_bf16_carry(c2.y, w[3] >> 16));
-                        pv[e / 2] = pack_upper(sr_bf16_carry(b2.x, w[0] & 0xFFFFu),
-                                               sr_bf16_carry(b2.y, w[1] & 0xFFFFu));
-                        pv[e / 2 + 1] = pack_upper(sr_bf16_carry(d2.x, w[2] & 0xFFFFu),
-                                                   sr_bf16_carry(d2.y, w[3] & 0xFFFFu));
-                    } else if (std::is_same_v<S, __half> &&
-                               fp16_normal(a2.x) && fp16_normal(a2.y) && fp16_normal(b2.x) &&
-                               fp16_normal(b2.y) && fp16_normal(c2.x) && fp16_normal(c2.y) &&
-                               fp16_normal(d2.x) && fp16_normal(d2.y)) {
-                        pu[e / 2] = pack(sr_f16_normal(a2.x, w[0] >> 16),
-                                         sr_f16_normal(a2.y, w[1] >> 16));
-                        pu[e / 2 + 1] = pack(sr_f16_normal(c2.x, w[2] >> 16),
-                                             sr_f16_normal(c2.y, w[3] >> 16));
-                        pv[e / 2] = pack(sr_f16_normal(b2.x, w[0] & 0xFFFFu),
-                                         sr_f16_normal(b2.y, w[1] & 0xFFFFu));
-                        pv[e / 2 + 1] = pack(sr_f16_normal(d2.x, w[2] & 0xFFFFu),
-                                             sr_f16_normal(d2.y, w[3] & 0xFFFFu));
-                    } else {
-                        pu[e / 2] = pack(quantize_sr<S>(a2.x, w[0]), quantize_sr<S>(a2.y, w[1]));
-                        pu[e / 2 + 1] = pack(quantize_sr<S>(c2.x, w[2]), quantize_sr<S>(c2.y, w[3]));
-                        pv[e / 2] = pack(quantize_sr<S>(b2.x, w[0] << 16),
-                                         quantize_sr<S>(b2.y, w[1] << 16));
-                        pv[e / 2 + 1] = pack(quantize_sr<S>(d2.x, w[2] << 16),
-                                             quantize_sr<S>(d2.y, w[3] << 16));
-                    }
-                }
-                if (col0 + VEC <= W) {
-                    if constexpr (VEC == 8) {
-                        st16(u1 + ro + col0, make_uint4(pu[0], pu[1], pu[2], pu[3]));
-                        st16(v1 + ro + col0, make_uint4(pv[0], pv[1], pv[2], pv[3]));
-                    } else {
-                        *reinterpret_cast<uint2*>(u1 + ro + col0) = make_uint2(pu[0], pu[1]);
-                        *reinterpret_cast<uint2*>(v1 + ro + col0) = make_uint2(pv[0], pv[1]);
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) {
-                        if (col0 + e < W) {
-                            const int sh = 16 * (e & 1);
-                            const unsigned short hu = (unsigned short)(pu[e / 2] >> sh);
-                            const unsigned short hv = (unsigned short)(pv[e / 2] >> sh);
-                            if constexpr (std::is_same_v<S, __nv_bfloat16>) {
-                                u1[ro + col0 + e] = __ushort_as_bfloat16(hu);
-                                v1[ro + col0 + e] = __ushort_as_bfloat16(hv);
-                            } else {
-                                u1[ro + col0 + e] = __ushort_as_half(hu);
-                                v1[ro + col0 + e] = __ushort_as_half(hv);
-                            }
-                        }
-                    }
-                }
-            }
+            if (act) sr_row<S, MODE, VEC>(un, uc, us, vv, ph, wl, er, col0, W, r, ro, u1, v1, m);
         } else if (act) {
             static_assert(VEC == Traits<S>::VEC, "16-byte vectors outside the stochastic rounding path");
             T ou[VEC], ov[VEC];
@@ -255,21 +266,6 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
                     T ea = (e == VEC - 1) ? er : uc[e + 1];
                     if (col0 + e >= W - 1) ea = uc[e];  // mirror at the east border
                     cell_update<MODE>(uc[e], w, ea, un[e], us[e], vv[e], ph[e], m, ou[e], ov[e]);
-                }
-            }
-            if constexpr ((MODE & MODE_SR) != 0) {
-                // stochastic rounding of the new state (index step0 + 1); a
-                // lane's VEC cells are VEC / 4 whole quads
-                static_assert(VEC % 4 == 0, "quads of cells");
-#pragma unroll
-                for (int e = 0; e < VEC; e += 4) {
-                    const Philox4 rb = sr_quad_bits(m.seed, (col0 + e) >> 2, r, m.step0 + 1);
-                    const unsigned w[4] = {rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        ou[e + i] = quantize_sr<S>(ou[e + i], w[i]);
-                        ov[e + i] = quantize_sr<S>(ov[e + i], w[i] << 16);
-                    }
                 }
             }
             if (col0 + VEC <= W) {
