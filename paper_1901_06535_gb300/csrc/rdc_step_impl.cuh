@@ -20,6 +20,7 @@
 //            launch of k_stepk give the same bits.
 #pragma once
 
+#include <mutex>
 #include <type_traits>
 
 #include "rdc_device.cuh"
@@ -526,13 +527,16 @@ template <typename S, int MODE>
 cudaError_t set_stepk_attr(size_t smem)
 {
     // Largest dynamic shared memory already granted, per device, per
-    // instantiation; raised monotonically.
+    // instantiation; raised monotonically, under a lock (separate handles may
+    // launch from several threads at once).
     static size_t configured[64] = {0};
+    static std::mutex mu;
     if (smem <= 48 * 1024) return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
     if (smem > configured[dev]) {
         e = cudaFuncSetAttribute(k_stepk<S, MODE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
