@@ -379,6 +379,15 @@ def main():
     bytes_per_launch = BYTES_PER_CELL[args.precision] * W * H
     achieved = bytes_per_launch / per_launch_s / 1e9
 
+    # end to end through the C ABI right after the timed region, on the same
+    # handle and under the same conditions (before the compute-heavy extras)
+    e2e = None
+    if not args.no_extras:
+        e2e_clocks = ClockSampler(local)
+        e2e_clocks.start()
+        e2e = _e2e(pkg, stream, h, disks, nE, args)
+        e2e["clocks"] = e2e_clocks.stop()
+
     extras = {}
     if rank == 0 and not args.no_extras:
         # temporal blocking and storage modes: effective GCUPS on the same grid
@@ -398,8 +407,6 @@ def main():
                   "batch_sweep": _batch_sweep(pkg, stream), "serving": _serving(pkg),
                   "serving_loaded": _serving_loaded(pkg),
                   "render": _render(pkg, stream, h)}
-    e2e = None if args.no_extras else _e2e(pkg, stream, h, disks, nE, args)
-
     pkg.rdc_destroy(h)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
