@@ -306,9 +306,25 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                         const float2 s2 =
                             bottom ? c2 : make_float2(P0[l - 1][e], P0[l - 1][e + 1]);
                         float2 un, vn;
-                        cell_update2<MODE>(c2, w2, e2, n2, s2,
-                                           make_float2(Q1[l - 1][e], Q1[l - 1][e + 1]),
-                                           make_float2(ph[e], ph[e + 1]), m, un, vn);
+                        if constexpr (sizeof(S) == 4 && !UK) {
+                            // FP32 storage, one grid: w + e as two scalar adds
+                            // into an aligned pair, not a paired add of the pairs
+                            // (w0, c0) and (c1, e1), which each need assembling by
+                            // moves: the same bits, fewer registers and
+                            // instructions (measured at 8192^2: K = 5 867 -> 934,
+                            // K = 6 864 -> 945 G cell-updates/s).  BF16 storage
+                            // lost 1 % at K = 4 and the batched kernel 1 % on the
+                            // 512-grid sweep; both keep the paired add.
+                            const float2 we2 = make_float2(__fadd_rn(w2.x, e2.x),
+                                                           __fadd_rn(w2.y, e2.y));
+                            cell_update2_we<MODE>(c2, we2, n2, s2,
+                                                  make_float2(Q1[l - 1][e], Q1[l - 1][e + 1]),
+                                                  make_float2(ph[e], ph[e + 1]), m, un, vn);
+                        } else {
+                            cell_update2<MODE>(c2, w2, e2, n2, s2,
+                                               make_float2(Q1[l - 1][e], Q1[l - 1][e + 1]),
+                                               make_float2(ph[e], ph[e + 1]), m, un, vn);
+                        }
                         if constexpr ((MODE & MODE_SR) != 0) {
                             // stochastic rounding of level l (state step0 + l);
                             // BF16 by the add-and-carry form (sr_bf16), a NaN
@@ -457,13 +473,17 @@ k_stepk_stream_capped(const S* __restrict__ u, const S* __restrict__ v,
 }
 
 // CTAs per SM the single-grid FP32 kernel is compiled for (0: the compiler's
-// choice).  Measured at 8192^2 (A/B, identical bits): K = 4 capped for 6 CTAs
-// (12 bytes spilled) 797 -> 807, K = 5 for 5 (24 bytes) 839 -> 860 G
-// cell-updates/s; K = 6 for 5 lost (72 bytes spilled, 857 -> 809).
+// choice).  Measured at 8192^2 (A/B, identical bits), with the horizontal sum
+// formed by scalar adds: K = 4 for 6 CTAs and K = 5 for 5 (78 and 92
+// registers, no spill), K = 6 left at 94 registers (5 CTAs); K = 8 capped for 4
+// (124 registers) 870 -> 895 G cell-updates/s; K = 5 for 6 (80 registers)
+// lost 938 -> 877 and K = 6 for 5 lost 949 -> 900.
 template <typename S, int MODE, int K>
 constexpr int stream_single_min_ctas()
 {
-    return (sizeof(S) != 4 || (MODE & MODE_SR) != 0) ? 0 : (K == 4 ? 6 : (K == 5 ? 5 : 0));
+    return (sizeof(S) != 4 || (MODE & MODE_SR) != 0)
+               ? 0
+               : (K == 4 ? 6 : (K == 5 ? 5 : (K == 8 ? 4 : 0)));
 }
 
 // Persistent k-step launch over a batch of grids (see k_step1_batch).
