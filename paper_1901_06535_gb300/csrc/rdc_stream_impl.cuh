@@ -306,15 +306,17 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                         const float2 s2 =
                             bottom ? c2 : make_float2(P0[l - 1][e], P0[l - 1][e + 1]);
                         float2 un, vn;
-                        if constexpr (sizeof(S) == 4 && !UK) {
-                            // FP32 storage, one grid: w + e as two scalar adds
-                            // into an aligned pair, not a paired add of the pairs
-                            // (w0, c0) and (c1, e1), which each need assembling by
-                            // moves: the same bits, fewer registers and
-                            // instructions (measured at 8192^2: K = 5 867 -> 934,
-                            // K = 6 864 -> 945 G cell-updates/s).  BF16 storage
-                            // lost 1 % at K = 4 and the batched kernel 1 % on the
-                            // 512-grid sweep; both keep the paired add.
+                        if constexpr (sizeof(S) == 4 && GHOST) {
+                            // mirrored ghost cells (FP32, K >= 4): w + e as two
+                            // scalar adds into an aligned pair, not a paired add
+                            // of the pairs (w0, c0) and (c1, e1), which each need
+                            // assembling by moves: the same bits, fewer registers
+                            // and instructions (measured at 8192^2: K = 5 867 ->
+                            // 934, K = 6 864 -> 945 G cell-updates/s; with it the
+                            // batched kernel takes the ghost cells too).  With
+                            // border selects (16-bit storage, K <= 3) the pairs
+                            // are formed by the selects anyway and the paired add
+                            // stays (BF16 lost 1 % at K = 4 with the scalar form).
                             const float2 we2 = make_float2(__fadd_rn(w2.x, e2.x),
                                                            __fadd_rn(w2.y, e2.y));
                             cell_update2_we<MODE>(c2, we2, n2, s2,
@@ -426,12 +428,12 @@ __device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __
     stream_warp_impl<S, MODE, K, N, GH, UK>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
 }
 
-// The single-grid FP32 kernel at K >= 4 (GH) takes the variants that
-// measured faster there: mirrored ghost cells instead of border selects
-// (K = 4: 724 -> 805, K = 6: 760 -> 786 G cell-updates/s at 8192^2), rows
-// two iterations ahead at K >= 5 and a six-fold unroll at K = 4; they were
-// slower for K <= 3, 16-bit storage and the batched kernel, whose register
-// budgets they exceed.
+// The FP32 kernels at K >= 4 (GH) take the variants that measured faster
+// there: mirrored ghost cells instead of border selects (K = 4: 724 -> 805,
+// K = 6: 760 -> 786 G cell-updates/s at 8192^2), rows two iterations ahead at
+// K >= 5 and a six-fold unroll at K = 4; they were slower for K <= 3 and
+// 16-bit storage, whose register budgets they exceed.  The batched kernel
+// takes them too since the scalar horizontal sum freed its registers.
 template <typename S, int K>
 constexpr bool stream_ghost() { return sizeof(S) == 4 && K >= 4; }
 
@@ -504,7 +506,10 @@ __device__ __forceinline__ void stream_batch_body(const GridDesc* __restrict__ d
         const int par = (d.par + j) & 1;
         Model<T> m = model_of<T>(d);
         m.step0 += sbase;
-        stream_warp<S, MODE, K, N, false, sizeof(S) == 4>(
+        // FP32 at K >= 4 with mirrored ghost cells, like the single-grid kernel
+        // (with the scalar horizontal sum they fit the register caps: the
+        // 512-grid sweep 834 -> 986 G cell-updates/s at K = 6)
+        stream_warp<S, MODE, K, N, sizeof(S) == 4 && K >= 4, sizeof(S) == 4>(
             static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
             static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, x0, y0, min(y0 + rows, d.H), m);
