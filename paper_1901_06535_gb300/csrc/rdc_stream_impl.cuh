@@ -306,17 +306,18 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                         const float2 s2 =
                             bottom ? c2 : make_float2(P0[l - 1][e], P0[l - 1][e + 1]);
                         float2 un, vn;
-                        if constexpr (sizeof(S) == 4 && GHOST) {
-                            // mirrored ghost cells (FP32, K >= 4): w + e as two
+                        if constexpr (GHOST) {
+                            // mirrored ghost cells (K >= 4): w + e as two
                             // scalar adds into an aligned pair, not a paired add
                             // of the pairs (w0, c0) and (c1, e1), which each need
                             // assembling by moves: the same bits, fewer registers
                             // and instructions (measured at 8192^2: K = 5 867 ->
                             // 934, K = 6 864 -> 945 G cell-updates/s; with it the
-                            // batched kernel takes the ghost cells too).  With
-                            // border selects (16-bit storage, K <= 3) the pairs
-                            // are formed by the selects anyway and the paired add
-                            // stays (BF16 lost 1 % at K = 4 with the scalar form).
+                            // batched FP32 kernel and the 16-bit storage kernels
+                            // take the ghost cells too).  With border selects
+                            // (K <= 3, stochastic rounding, the batched 16-bit
+                            // kernel) the pairs are formed by the selects anyway
+                            // and the paired add stays.
                             const float2 we2 = make_float2(__fadd_rn(w2.x, e2.x),
                                                            __fadd_rn(w2.y, e2.y));
                             cell_update2_we<MODE>(c2, we2, n2, s2,
@@ -428,14 +429,21 @@ __device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __
     stream_warp_impl<S, MODE, K, N, GH, UK>(u, v, phi, u1, v1, W, H, pitch, col_out, y0, y1, m);
 }
 
-// The FP32 kernels at K >= 4 (GH) take the variants that measured faster
-// there: mirrored ghost cells instead of border selects (K = 4: 724 -> 805,
-// K = 6: 760 -> 786 G cell-updates/s at 8192^2), rows two iterations ahead at
-// K >= 5 and a six-fold unroll at K = 4; they were slower for K <= 3 and
-// 16-bit storage, whose register budgets they exceed.  The batched kernel
-// takes them too since the scalar horizontal sum freed its registers.
-template <typename S, int K>
-constexpr bool stream_ghost() { return sizeof(S) == 4 && K >= 4; }
+// The single-grid kernels at K >= 4 (GH) take the variants that measured
+// faster there: mirrored ghost cells instead of border selects (FP32 K = 4:
+// 724 -> 805, K = 6: 760 -> 786 G cell-updates/s at 8192^2), rows two
+// iterations ahead at K >= 5 and a six-fold unroll at K = 4; they were slower
+// for K <= 3, whose four cells per lane leave no registers.  16-bit storage
+// takes them since the scalar horizontal sum freed its registers (BF16 K = 4
+// 666 -> 720, K = 6 611 -> 698; FP16 703 -> 748, 644 -> 741); with stochastic
+// rounding the ghost cells would draw random words of their own, so those
+// kernels keep the border selects and their own unrolling.  The batched FP32
+// kernel takes them as well (stream_batch_body).  FP64 keeps the selects.
+template <typename S, int MODE, int K>
+constexpr bool stream_ghost()
+{
+    return sizeof(typename Traits<S>::T) == 4 && K >= 4 && (MODE & MODE_SR) == 0;
+}
 
 template <typename S, int MODE, int K, int N>
 __device__ __forceinline__ void stepk_stream_body(const S* __restrict__ u, const S* __restrict__ v,
@@ -449,7 +457,7 @@ __device__ __forceinline__ void stepk_stream_body(const S* __restrict__ u, const
     const int wx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (wx >= nwarps_x) return;                       // whole warps only
     const int y0 = blockIdx.y * rows;
-    stream_warp<S, MODE, K, N, stream_ghost<S, K>()>(u, v, phi, u1, v1, W, H, pitch, wx * G::OUTC, y0,
+    stream_warp<S, MODE, K, N, stream_ghost<S, MODE, K>()>(u, v, phi, u1, v1, W, H, pitch, wx * G::OUTC, y0,
                                min(y0 + rows, H), m);
 }
 

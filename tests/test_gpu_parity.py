@@ -118,14 +118,15 @@ def test_kblock_bitwise(gpu, prec, k, W, H, variant):
 @pytest.mark.parametrize("W,H", [(1, 1), (2, 3), (3, 2), (5, 5), (6, 13), (13, 6), (17, 3),
                                  (64, 2), (2, 64)])
 @pytest.mark.parametrize("krows", [1, 3, 29])
-def test_kblock_mirrored_ghosts_tiny_grids(gpu, k, W, H, krows):
-    """The FP32 streamed kernel for K >= 4 loads mirrored ghost rows and
-    columns instead of selecting at the borders; grids narrower or shorter
+@pytest.mark.parametrize("prec", ["f32", "bf16", "f16"])
+def test_kblock_mirrored_ghosts_tiny_grids(gpu, k, W, H, krows, prec):
+    """The streamed kernel for K >= 4 (FP32 compute) loads mirrored ghost rows
+    and columns instead of selecting at the borders; grids narrower or shorter
     than the K-cell reach reflect more than once.  Bits equal single steps."""
     seeds = [(W / 2, H / 2, max(1.0, min(W, H) / 3), 0.8)]
     n = 3 * k + 1
-    a, av, _ = gpu_run(gpu, W, H, seeds=seeds, n=n, prec="f32", k=1)
-    b, bv, _ = gpu_run(gpu, W, H, seeds=seeds, n=n, prec="f32", k=k,
+    a, av, _ = gpu_run(gpu, W, H, seeds=seeds, n=n, prec=prec, k=1)
+    b, bv, _ = gpu_run(gpu, W, H, seeds=seeds, n=n, prec=prec, k=k,
                        shape=dict(variant=0, krows=krows))
     assert np.array_equal(a, b) and np.array_equal(av, bv)
 
