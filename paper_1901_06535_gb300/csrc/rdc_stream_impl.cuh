@@ -313,11 +313,10 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
                             // assembling by moves: the same bits, fewer registers
                             // and instructions (measured at 8192^2: K = 5 867 ->
                             // 934, K = 6 864 -> 945 G cell-updates/s; with it the
-                            // batched FP32 kernel and the 16-bit storage kernels
-                            // take the ghost cells too).  With border selects
-                            // (K <= 3, stochastic rounding, the batched 16-bit
-                            // kernel) the pairs are formed by the selects anyway
-                            // and the paired add stays.
+                            // batched kernel and the 16-bit storage kernels take
+                            // the ghost cells too).  With border selects (K <= 3,
+                            // stochastic rounding) the pairs are formed by the
+                            // selects anyway and the paired add stays.
                             const float2 we2 = make_float2(__fadd_rn(w2.x, e2.x),
                                                            __fadd_rn(w2.y, e2.y));
                             cell_update2_we<MODE>(c2, we2, n2, s2,
@@ -437,7 +436,7 @@ __device__ __forceinline__ void stream_warp(const S* __restrict__ u, const S* __
 // takes them since the scalar horizontal sum freed its registers (BF16 K = 4
 // 666 -> 720, K = 6 611 -> 698; FP16 703 -> 748, 644 -> 741); with stochastic
 // rounding the ghost cells would draw random words of their own, so those
-// kernels keep the border selects and their own unrolling.  The batched FP32
+// kernels keep the border selects and their own unrolling.  The batched
 // kernel takes them as well (stream_batch_body).  FP64 keeps the selects.
 template <typename S, int MODE, int K>
 constexpr bool stream_ghost()
@@ -514,10 +513,11 @@ __device__ __forceinline__ void stream_batch_body(const GridDesc* __restrict__ d
         const int par = (d.par + j) & 1;
         Model<T> m = model_of<T>(d);
         m.step0 += sbase;
-        // FP32 at K >= 4 with mirrored ghost cells, like the single-grid kernel
-        // (with the scalar horizontal sum they fit the register caps: the
-        // 512-grid sweep 834 -> 986 G cell-updates/s at K = 6)
-        stream_warp<S, MODE, K, N, sizeof(S) == 4 && K >= 4, sizeof(S) == 4>(
+        // mirrored ghost cells where the single-grid kernel takes them (with the
+        // scalar horizontal sum they fit the register caps: the 512-grid FP32
+        // sweep 834 -> 986 G cell-updates/s at K = 6; 128 grids at K = 6 with
+        // BF16 storage 580 -> 616, FP16 589 -> 634)
+        stream_warp<S, MODE, K, N, stream_ghost<S, MODE, K>(), sizeof(S) == 4>(
             static_cast<const S*>(d.u[par]), static_cast<const S*>(d.v[par]),
             static_cast<const PhiT*>(d.phi), static_cast<S*>(d.u[par ^ 1]),
             static_cast<S*>(d.v[par ^ 1]), d.W, d.H, d.pitch, x0, y0, min(y0 + rows, d.H), m);
