@@ -30,11 +30,13 @@ namespace rdc {
 // Unroll factor of the streamed kernel's row loop: the three-row register
 // rotation and the K-deep phi queue become renaming when it is a multiple of
 // both.  Measured at 8192^2 (A/B, identical bits), the single-grid FP32
-// kernel (GH) runs best at K = 5 unrolled 5 times (809 -> 860 G
-// cell-updates/s), K = 6 6 times (809 -> 852), K = 7 7 times (749 -> 771),
-// K = 8 8 times (735 -> 757), K = 4 6 times (12 lost 7 %); the FP32 batched
-// kernel (UK) at K = 6 six times (512-grid sweep: 813 -> 834); the rest three
-// times from K = 4 (K times lost 9 % with BF16 storage at K = 6).
+// kernel with ghost cells (GH) runs best at K = 5 unrolled 5 times (809 -> 860
+// G cell-updates/s; with the scalar horizontal sum 6 times lost 940 -> 913, 3
+// times 898), K = 6 6 times (809 -> 852), K = 7 7 times (749 -> 771), K = 8 8
+// times (735 -> 757), K = 4 6 times (12 lost 7 %).  The kernels with ghost
+// cells (FP32 compute at K >= 4 without stochastic rounding, batched or not)
+// take these; with border selects the batched FP32 kernel (UK) runs K = 6 six
+// times (512-grid sweep: 813 -> 834) and the rest three times from K = 4.
 template <int K, bool GH, bool UK>
 constexpr int stream_unroll()
 {
@@ -192,9 +194,10 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     // Row t's u, v and phi are loaded DIST iterations ahead of their first use
     // (level 1 needs row t at once, and rows stream from HBM).  Measured at
     // 8192^2: one row ahead +25 % at K = 3 and +11 % at K = 6 (FP32); two rows
-    // ahead another +6 % for the single-grid FP32 kernel at K >= 5 (GH), but
-    // -9 % with 16-bit storage and -4 % in the batched kernel; none at K = 2,
-    // whose four cells per lane leave no registers (-14 %).
+    // ahead another +6 % for the single-grid FP32 kernel at K >= 5 (GH; with
+    // border selects it lost 9 % with 16-bit storage and 4 % in the batched
+    // kernel, which now take the ghost cells and this distance with them);
+    // none at K = 2, whose four cells per lane leave no registers (-14 %).
     constexpr int DIST = (GH && K >= 5) ? 2 : (K >= 3 ? 1 : 0);
     T pu[N], pv[N], pp[N], qu[N], qv[N], qp[N];
 #pragma unroll
@@ -202,10 +205,10 @@ __device__ __forceinline__ void stream_warp_impl(const S* __restrict__ u,
     if constexpr (DIST >= 1) load_row(t0, pu, pv, pp);
     if constexpr (DIST >= 2)
         if (t0 + 1 <= t_end) load_row(t0 + 1, qu, qv, qp);
-    // Unrolled row loop: the three-row rotation becomes renaming; the
-    // single-grid FP32 kernel at K = 4 (GH) runs best unrolled six times
-    // (835 vs 813 G cell-updates/s; six times lost 17 % with 16-bit storage
-    // and 3 % in the batched kernel).
+    // Unrolled row loop: the three-row rotation becomes renaming; the kernels
+    // with ghost cells at K = 4 (GH) run best unrolled six times (single-grid
+    // FP32 835 vs 813 G cell-updates/s; with border selects six times lost
+    // 17 % with 16-bit storage and 3 % in the batched kernel).
     constexpr int UNROLL = stream_unroll<K, GH, UK>();
 #pragma unroll UNROLL
     for (int t = t0; t <= t_end; ++t) {
