@@ -436,8 +436,7 @@ int rdc_get_view(rdc_sim* sim, rdc_view* out);
 typedef struct {
     int32_t bx;        /* single-step kernel: threads per CTA along x, a
                           multiple of 32 in [32, 256]; each thread owns one
-                          16-byte vector of cells (4 FP32, 2 FP64, 8 BF16/FP16;
-                          with RDC_STOCH_ROUND, BF16 takes 4 cells, 8 bytes) */
+                          16-byte vector of cells (4 FP32, 2 FP64, 8 BF16/FP16) */
     int32_t rows;      /* single-step kernel: rows marched per CTA, >= 1 */
     int32_t tx, ty;    /* temporally blocked kernel: interior tile, >= 1 each */
     int32_t nthreads;  /* temporally blocked kernel: threads per CTA, a

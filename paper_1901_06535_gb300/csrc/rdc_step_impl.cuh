@@ -83,13 +83,15 @@ __device__ __forceinline__ void vload(const S* p, typename Traits<S>::T (&o)[VEC
     }
 }
 
-// Cells per lane of the single-step kernel: one 16-byte vector, except for
-// BF16 with stochastic rounding, which takes one quad (8 bytes) per lane: its
-// random words and rounding then leave room for more resident warps.
+// Cells per lane of the single-step kernel: one 16-byte vector (with
+// stochastic rounding two quads, computed and rounded one after the other).
+// One quad (8 bytes) per lane was tried for stochastic rounding to leave room
+// for more resident warps; at 8192^2 the 16-byte vectors at 72 registers are
+// faster (BF16 399 -> 416, FP16 363 -> 397 G cell-updates/s, identical bits).
 template <typename S, int MODE>
 constexpr int step1_vec()
 {
-    return ((MODE & MODE_SR) != 0 && sizeof(S) == 2) ? 4 : Traits<S>::VEC;
+    return Traits<S>::VEC;
 }
 
 // One row of a lane's VEC cells (VEC / 4 whole quads) of a single Euler step
@@ -290,22 +292,14 @@ __device__ __forceinline__ void step1_warp(const S* __restrict__ u, const S* __r
     }
 }
 
-// Register caps: at most 72 registers, so that the 16-bit-storage
-// instantiations (8 cells per thread) fit 7 CTAs per SM; with stochastic
-// rounding (4 cells per thread) BF16 and FP16 are capped at RDC_SR_BF16_REGS
-// and RDC_SR_F16_REGS.
-#ifndef RDC_SR_BF16_REGS
-#define RDC_SR_BF16_REGS 64
-#endif
-#ifndef RDC_SR_F16_REGS
-#define RDC_SR_F16_REGS 64
-#endif
+// Register cap: at most 72 registers, so that the 16-bit-storage
+// instantiations (8 cells per thread) fit 7 CTAs per SM, with stochastic
+// rounding too (BF16 spills 76 bytes there and is still faster than at 80 or
+// 96 registers: 416 against 406 and 386 G cell-updates/s at 8192^2).
 template <typename S, int MODE>
 constexpr int step1_max_regs()
 {
-    return (MODE & MODE_SR) == 0 ? 72
-                                 : (std::is_same_v<S, __nv_bfloat16> ? RDC_SR_BF16_REGS
-                                                                     : RDC_SR_F16_REGS);
+    return 72;
 }
 
 template <typename S, int MODE>
