@@ -98,3 +98,15 @@ def test_row_copies_refuse_null_sim(librdc):
     for fn in (L.rdc_get_rows, L.rdc_put_rows):
         assert fn(None, 0, 1, buf, buf, 0) == librdc.RDC_EINVAL
         assert fn(None, 0, 0, None, None, 0) == librdc.RDC_EINVAL
+
+
+def test_strip_grid_refuses_before_touching_the_device(librdc):
+    """Stochastic rounding and a halo wider than a strip are refused before
+    any simulation is created (no device needed)."""
+    from paper_1901_06535_gb300.strips import StripGrid
+    with pytest.raises(ValueError):
+        StripGrid(64, 64, 2, precision="bf16", flags=librdc.RDC_STOCH_ROUND, round_seed=3)
+    with pytest.raises(ValueError):
+        StripGrid(64, 10, 3, halo=4)                 # strips of 3 and 4 rows
+    with pytest.raises(ValueError):
+        StripGrid(64, 64, 2, phi=np.zeros((63, 64), np.float32))
